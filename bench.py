@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: F over all N slices of one parareal iteration.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config 3]
+
+One step = one pr_fine_all_slices call on the whole batch of slices of the
+chosen synthetic workload (default: the 2D discontinuous-inclusion problem,
+1024^2 fine grid, 64 slices, m_F = 384 fine steps per slice).  The metric is
+fine grid-point updates per second, slices * m_F * n^2 / time, whole job.
+Inputs are resident in HBM and larger than L2 (0.54 GB per rank), so no L2
+flush is needed between steps.
+
+Besides `value` the JSON line carries
+  * roofline  -- the fused pass kernel's algorithmic bytes (20 B per point
+                 per pass: read u, u_t, kappa, write u, u_t in FP32) over its
+                 mean launch time, timed with CUDA events on its stream,
+                 against the measured HBM copy bandwidth;
+  * e2e       -- the same metric through the C ABI with the slices coming from
+                 pinned host memory and going back to it every step;
+  * cpu_baseline -- the FP64 oracle on a bounded sample of the same workload
+                 on the host cores (parallel over slices, like the paper's
+                 parFor);
+  * clocks    -- nvidia-smi samples taken during the timed region.
+With --impl reference the oracle itself is the timed arm (bounded sample per
+step).  Multi-GPU (torchrun): every rank propagates its own copy of the
+workload (slices are independent units; weak scaling, no collective on the
+data path); time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1905_00473_gb300 import workloads as W  # noqa: E402
+
+ALGO_BYTES_PER_POINT_PASS = 20  # read u, u_t, kappa + write u, u_t (FP32)
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------- CPU oracle
+def _oracle_task(args):
+    u, v, c, dt, steps, dx = args
+    from oracle import fine
+    t0 = time.perf_counter()
+    fine.velocity_verlet(u, v, c, dt, steps, dx)
+    return time.perf_counter() - t0
+
+
+def _warm(_):
+    import oracle.fine  # noqa: F401
+    return 0
+
+
+class OracleSampler:
+    """The FP64 oracle on `procs` host processes, one slice per process."""
+
+    def __init__(self, w: W.Workload, procs: int, steps: int):
+        self.w, self.procs, self.steps = w, procs, steps
+        u, v = W.slice_states(w, n_slices=procs, seed=11)
+        self.tasks = [(u[i], v[i], w.c, w.dt_f, steps, w.dx_f) for i in range(procs)]
+        self.pool = mp.get_context("spawn").Pool(procs)
+        self.pool.map(_warm, range(procs))
+
+    def run(self) -> tuple[float, float]:
+        """(point-updates, wall seconds) of one sample."""
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_task, self.tasks, chunksize=1)
+        wall = time.perf_counter() - t0
+        return self.procs * self.steps * self.w.points, wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def describe(self) -> str:
+        return (f"{self.procs} slices x {self.steps} of {self.w.m_f} fine steps of "
+                f"{self.w.name}, one slice per process")
+
+
+def oracle_procs() -> int:
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows: list[list[str]] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        for r in self.rows:
+            if len(r) < 8:
+                continue
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, r[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peak() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_1905_00473_gb300/csrc/fine_tb2d.cu", "paper_1905_00473_gb300/csrc/pr_internal.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload_key: str):
+    """DRAM bytes per fused launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "fine_tb2d_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("per_launch_bytes", {}).get(workload_key)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_for(cfg: str) -> W.Workload:
+    if cfg not in ("2", "3"):
+        raise SystemExit("--config must be 2 or 3 (2D FP32 sweeps)")
+    return W.CONFIGS[cfg]()
+
+
+def workload_desc(w: W.Workload) -> dict:
+    return {"workload": w.name, "dim": w.dim, "n_fine": w.n_fine, "slices": w.n_slices,
+            "m_f": w.m_f, "point_updates_per_step": w.point_steps_per_sweep(),
+            "inputs": "seeded Gaussian-pulse slice states, c field of the configuration",
+            "l2": "inputs larger than L2 (no flush)"}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(a) -> int:
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload_for(a.config)
+    procs = oracle_procs()
+    steps_per_sample = max(4, min(w.m_f, 64))
+    smp = OracleSampler(w, procs, steps_per_sample)
+    try:
+        for _ in range(a.warmup):
+            smp.run()
+        tot_pts, tot_t = 0, 0.0
+        for _ in range(a.steps):
+            p, t = smp.run()
+            tot_pts += p
+            tot_t += t
+    finally:
+        smp.close()
+    value = tot_pts / tot_t
+    line = {
+        "impl": "reference", "metric": "fine grid-point updates/s", "value": value,
+        "unit": "point-updates/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * tot_t / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_desc(w), parallelism="host processes over slices"),
+        "cpu_baseline": {"value": value, "unit": "point-updates/s", "cores": procs,
+                         "kind": "oracle", "sample": smp.describe() + " per step"},
+        "e2e": {"value": value, "unit": "point-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(a) -> int:
+    rank, world, local = dist_env()
+    w = workload_for(a.config)
+    # the oracle pool is spawned before any CUDA call
+    smp = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        smp = OracleSampler(w, oracle_procs(), max(4, min(w.m_f, 64)))
+
+    import torch
+    from paper_1905_00473_gb300 import binding
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    u_h, v_h = W.slice_states(w, seed=rank)
+    u_pin = torch.from_numpy(u_h.astype("float32")).pin_memory()
+    v_pin = torch.from_numpy(v_h.astype("float32")).pin_memory()
+    c = torch.tensor(w.c, dtype=torch.float32, device=dev)
+    ctx = binding.pr_create(w.dim, w.n_fine, w.ratio, c, w.dt_f, w.dt_c, w.n_slices, w.t_final,
+                            block_depth=a.block_depth)
+    info = binding.pr_info(ctx)
+    u_in = u_pin.to(dev)
+    v_in = v_pin.to(dev)
+    u_out = torch.empty_like(u_in)
+    v_out = torch.empty_like(v_in)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(a.warmup):
+        binding.pr_fine_all_slices(ctx, u_in, v_in, u_out, v_out)
+    binding.pr_check(ctx)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    binding.pr_profile(ctx, True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        binding.pr_fine_all_slices(ctx, u_in, v_in, u_out, v_out)
+    ev1.record(stream)
+    barrier()
+    binding.pr_profile(ctx, False)
+    clk = clocks.stop()
+    binding.pr_check(ctx)
+    ms = ev0.elapsed_time(ev1)
+    fused_n, fused_ms = binding.pr_profile_read(ctx, 0)
+    single_n, single_ms = binding.pr_profile_read(ctx, 1)
+    if pg is not None:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    units = w.point_steps_per_sweep()
+    value = world * units * a.steps / (ms * 1e-3)
+
+    # end to end through the C ABI: pinned host -> device -> F -> host
+    u_back = torch.empty_like(u_pin).pin_memory()
+    v_back = torch.empty_like(v_pin).pin_memory()
+    e2e_steps = max(3, min(a.steps, 20))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        u_in.copy_(u_pin, non_blocking=True)
+        v_in.copy_(v_pin, non_blocking=True)
+        binding.pr_fine_all_slices(ctx, u_in, v_in, u_out, v_out)
+        u_back.copy_(u_out, non_blocking=True)
+        v_back.copy_(v_out, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if pg is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * units * e2e_steps / (e2e_ms * 1e-3)
+    io_bytes = 2 * u_pin.numel() * 4
+
+    # roofline of the dominant kernel (fused pass when present)
+    peak, peak_src = measured_peak()
+    if fused_n > 0:
+        kname, launches, kms = "fine_tb2d_kernel", fused_n, fused_ms
+        levels_per_launch = info["block_depth"]
+    else:
+        kname, launches, kms = "level_f32 (one level per launch)", single_n, single_ms
+        levels_per_launch = 1
+    per_launch_bytes = ALGO_BYTES_PER_POINT_PASS * w.points * w.n_slices
+    avg_ms = kms / max(1, launches)
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src,
+            "traffic": ncu_traffic(w.name) if fused_n > 0 else None,
+            "algorithmic_bytes_per_launch": per_launch_bytes,
+            "levels_per_launch": levels_per_launch, "mean_launch_ms": avg_ms,
+            "launch_share": kms / ms if ms > 0 else None}
+
+    cpu = None
+    if smp is not None:
+        try:
+            p, t = smp.run()
+            cpu = {"value": p / t, "unit": "point-updates/s", "cores": smp.procs,
+                   "kind": "oracle", "sample": smp.describe()}
+        finally:
+            smp.close()
+
+    if rank == 0:
+        line = {
+            "metric": "fine grid-point updates/s", "value": value, "unit": "point-updates/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": dict(workload_desc(w), block_depth=info["block_depth"],
+                           parallelism=f"replica per GPU x{world}"),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "point-updates/s", "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes, "steps": e2e_steps},
+            "gpu_launches": fused_n + single_n,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="3")
+    ap.add_argument("--block-depth", type=int, default=0, help="0 = library default")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args(argv)
+    if a.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

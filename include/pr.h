@@ -1,0 +1,158 @@
+/*
+ * pr.h -- C ABI of the GB300 parallel-in-time wave propagator.
+ *
+ * The library implements the data-parallel hot path of the stable
+ * parareal-like method of Nguyen & Tsai, "A stable parareal-like method for
+ * the second order wave equation" (arXiv 1905.00473): the fine propagator F
+ * applied independently to every time slice of one parareal iteration
+ * (Alg. 3, the parFor over n), for
+ *
+ *     u_tt = c(x)^2 Lap u  on the periodic unit box [0,1)^d   (Sec. 1, eq. waveequation)
+ *
+ * discretised, as in Sec. 3.1, by the 2nd-order central-difference Laplacian
+ * on a uniform grid and velocity Verlet in time.
+ *
+ * Conventions shared by every entry point
+ *  - All array arguments are DEVICE pointers on the context's device, in the
+ *    context's dtype (float for PR_F32, double for PR_F64), unless stated.
+ *  - A field on an n^d grid is stored row-major with x fastest:
+ *    [z][y][x] (3D), [y][x] (2D), [x] (1D); "pts" = n^d.
+ *    A batch of slices is [N][pts], slice-contiguous.
+ *  - Pointers must be 16-byte aligned (torch allocations are).
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream) and is asynchronous w.r.t. the host.  Caller
+ *    buffers are borrowed for the duration of the enqueued work.
+ *  - No exception or abort crosses the ABI.  Every call returns a pr_status;
+ *    on failure pr_last_error() holds a message.  Invalid arguments are
+ *    rejected with PR_EINVAL before anything is launched.
+ *  - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef PR_H
+#define PR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pr_status {
+    PR_OK = 0,
+    PR_EINVAL = 1,      /* invalid argument; nothing was launched */
+    PR_ENOMEM = 2,      /* device allocation failed */
+    PR_ECUDA = 3,       /* a CUDA runtime call or a launch failed */
+    PR_ETIMEOUT = 4,    /* a bounded device-side wait gave up (see pr_check) */
+    PR_EUNSTABLE = 5,   /* reserved: energy growth beyond the stability bound */
+    PR_ENOTCONV = 6     /* reserved: iteration did not reach its tolerance */
+} pr_status;
+
+typedef enum pr_dtype { PR_F32 = 0, PR_F64 = 1 } pr_dtype;
+
+/* Fine grid of the periodic unit box.  dim in {1,2,3}; nf[0..dim-1] are the
+ * fine points per axis (x, y, z) and must be equal (dx = 1/nf on every axis,
+ * Sec. 3.1 "uniform Cartesian grids"); ratio = coarse spacing / fine spacing
+ * (coarse nodes coincide with fine nodes, Sec. 6), nf % ratio == 0. */
+typedef struct pr_grid {
+    int dim;
+    int64_t nf[3];
+    int ratio;
+} pr_grid;
+
+/* Options.  block_depth: fine steps fused per HBM pass of the 2D FP32 kernel
+ * (0 = library default; 1 = one step per pass).  Other fields are reserved
+ * for the coarse/correction stages and are ignored by the fine path. */
+typedef struct pr_options {
+    int dtype;          /* pr_dtype */
+    int grad_order;     /* 2, 4, 6, 8 or 0 = spectral (nabla_h, Sec. 6.4) */
+    int interp;         /* 0 = Fourier (interpft, Sec. 6) */
+    double tol;         /* rank tolerance of Alg. 1 */
+    int block_depth;
+    int max_iters;
+} pr_options;
+
+typedef struct pr_ctx pr_ctx;
+
+/* pr_create -- set up one problem (Sec. 3.1: grids, steps, medium).
+ *
+ *  grid   fine grid (see pr_grid).
+ *  c_dev  DEVICE pointer, dtype of opts->dtype, nf^dim wave-speed values
+ *         c(x_j) > 0 at the fine nodes.  Read during the call only; the
+ *         context keeps its own coefficient array kappa_j = c_j^2 dt_f/dx^2.
+ *  dt_f   fine step delta t; dt_c coarse step Delta t.
+ *  N      number of time slices (coupling intervals); T final time.
+ *         Delta t_com = T/N.  m_F = Delta t_com/dt_f and m_C = Delta t_com/dt_c
+ *         must be integers (Sec. 3.1, "m_F, m_C in N"), within 1e-9 relative.
+ *  opts   may be NULL (defaults: F32, 4th-order nabla_h, Fourier I, tol 1e-13).
+ *  out    receives the context.
+ *
+ * Checks the CFL condition of the Verlet/central-difference pair,
+ * max c * dt * sqrt(dim) / dx <= 1, on both grids (PR_EINVAL if violated).
+ * Synchronises the device (it reads max c back).
+ */
+pr_status pr_create(const pr_grid* grid, const void* c_dev, double dt_f, double dt_c, int N,
+                    double T, const pr_options* opts, pr_ctx** out);
+
+/* pr_destroy -- free the context and all device memory it owns (NULL is a no-op). */
+void pr_destroy(pr_ctx* ctx);
+
+/* pr_last_error -- message of the last failing call on ctx (never NULL).
+ * With ctx == NULL returns the last error of pr_create on this thread. */
+const char* pr_last_error(const pr_ctx* ctx);
+
+/* pr_fine_all_slices -- the fine propagator F on a batch of slices
+ * (Alg. 3: [v_n, v_t n] = F[u^k_{n-1}, u_t^k_{n-1}] for all n, in parallel).
+ *
+ *  u_in, v_in    [N][pts] displacement u and velocity u_t at the start of
+ *                each slice.
+ *  u_out, v_out  [N][pts] results after m_F velocity-Verlet steps of dt_f
+ *                (one coupling interval Delta t_com).
+ *  n_begin,n_end slices [n_begin, n_end) are propagated, 0 <= n_begin <= n_end <= N;
+ *                other slices of the outputs are not touched.
+ *  stream        cudaStream_t.
+ * out == in (u_out == u_in and v_out == v_in) is allowed; any other overlap
+ * between inputs and outputs is rejected (PR_EINVAL).  Slices are
+ * independent: out[n] depends on in[n] only.  Uses context-owned scratch
+ * (allocated at pr_create).  Device-side wait time-outs are reported by
+ * pr_check, not by this call.
+ */
+pr_status pr_fine_all_slices(pr_ctx* ctx, const void* u_in, const void* v_in, void* u_out,
+                             void* v_out, int n_begin, int n_end, void* stream);
+
+/* pr_check -- synchronise `stream`, then report and clear a device-side error
+ * flag set by a kernel whose bounded wait gave up (PR_ETIMEOUT), or a pending
+ * CUDA error (PR_ECUDA). */
+pr_status pr_check(pr_ctx* ctx, void* stream);
+
+/* pr_info -- derived constants of the context (any pointer may be NULL):
+ * m_F, m_C, the number of fine points per slice, and the fine step count per
+ * HBM pass the fine propagator uses. */
+pr_status pr_info(const pr_ctx* ctx, int* m_f, int* m_c, int64_t* pts, int* block_depth);
+
+/* pr_energy -- discrete wave energy of every slice (Sec. 3.1, eq.
+ * discrete-wave-energy) on the fine grid, accumulated in FP64:
+ *   E_n = 1/2 sum_j |nabla_h u_n(x_j)|^2 dx^d + 1/2 sum_j c_j^-2 |v_n(x_j)|^2 dx^d
+ * with nabla_h the 4th-order central difference (Sec. 6.4, "4 order").
+ *  u, v     [N][pts] device arrays (dtype), slices [n_begin, n_end) are read.
+ *  e_host   HOST array of n_end - n_begin doubles receiving E_n.
+ * Synchronises `stream` before returning. */
+pr_status pr_energy(pr_ctx* ctx, const void* u, const void* v, int n_begin, int n_end,
+                    double* e_host, void* stream);
+
+/* pr_profile -- per-launch timing of the fine propagator with CUDA events
+ * recorded on the launching stream (the per-phase timers of the paper's
+ * Sec. 7.2.4 timing study, at kernel granularity).  on != 0 clears the record
+ * and starts recording an event pair around every kernel that
+ * pr_fine_all_slices launches; on == 0 stops recording. */
+pr_status pr_profile(pr_ctx* ctx, int on);
+
+/* pr_profile_read -- synchronise on the recorded events and report, for
+ * kernel kind 0 (fused multi-level pass) or 1 (single-level pass), the number
+ * of launches recorded and their summed duration in milliseconds. */
+pr_status pr_profile_read(pr_ctx* ctx, int kind, int* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PR_H */

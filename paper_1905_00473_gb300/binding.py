@@ -1,0 +1,188 @@
+"""Thin ctypes binding of the C ABI in include/pr.h (argument marshalling only).
+
+Every function keeps the C name.  Arrays are torch tensors on the context's
+CUDA device; the binding checks their device, dtype, contiguity and size,
+passes data_ptr() and the current CUDA stream, and raises PrError on a
+non-zero status.  All computation happens in the CUDA library; if it cannot be
+loaded the import fails loudly (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+LIB_PATH = os.path.join(PKG, "_lib", "libpr.so")
+HEADER = os.path.join(ROOT, "include", "pr.h")
+
+PR_F32, PR_F64 = 0, 1
+STATUS = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOMEM", 3: "PR_ECUDA", 4: "PR_ETIMEOUT",
+          5: "PR_EUNSTABLE", 6: "PR_ENOTCONV"}
+
+
+class PrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pr_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nf", ctypes.c_int64 * 3), ("ratio", ctypes.c_int)]
+
+
+class pr_options(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("grad_order", ctypes.c_int), ("interp", ctypes.c_int),
+                ("tol", ctypes.c_double), ("block_depth", ctypes.c_int), ("max_iters", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "pr_create": (ctypes.c_int, [ctypes.POINTER(pr_grid), _P, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_double, ctypes.POINTER(pr_options),
+                                 ctypes.POINTER(_P)]),
+    "pr_destroy": (None, [_P]),
+    "pr_last_error": (ctypes.c_char_p, [_P]),
+    "pr_fine_all_slices": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
+    "pr_check": (ctypes.c_int, [_P, _P]),
+    "pr_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
+    "pr_energy": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_double), _P]),
+    "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_double)]),
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def declared_symbols() -> list[str]:
+    """Entry points declared in include/pr.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(pr_\w+)\s*\(", text, flags=re.M)))
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libpr.so (built by paper_1905_00473_gb300.build) and bind signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libpr.so not built at {path}: run `python -m paper_1905_00473_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _check(status: int, ctx_ptr) -> None:
+    if status != 0:
+        msg = load().pr_last_error(ctx_ptr)
+        raise PrError(status, msg.decode() if msg else "")
+
+
+class Context:
+    """Owns a pr_ctx; methods mirror the C entry points that take a context."""
+
+    def __init__(self, handle: int, dim: int, n: int, N: int, dtype: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.dim, self.n, self.N, self.dtype = dim, n, N, dtype
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().pr_destroy(self.handle)
+                self.handle = ctypes.c_void_p(None)
+        except Exception:
+            pass
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float32 if self.dtype == PR_F32 else torch.float64
+
+    def _arr(self, t, name: str):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.torch_dtype:
+            raise TypeError(f"{name} must be {self.torch_dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() != self.N * self.n ** self.dim:
+            raise ValueError(f"{name} must hold N * n^dim = {self.N * self.n ** self.dim} values")
+        return ctypes.c_void_p(t.data_ptr())
+
+
+def pr_create(dim: int, n: int, ratio: int, c, dt_f: float, dt_c: float, N: int, T: float,
+              dtype: int = PR_F32, block_depth: int = 0, grad_order: int = 4,
+              tol: float = 1e-13) -> Context:
+    import torch
+    lib = load()
+    if not isinstance(c, torch.Tensor) or not c.is_cuda or not c.is_contiguous():
+        raise TypeError("c must be a contiguous CUDA tensor")
+    want = torch.float32 if dtype == PR_F32 else torch.float64
+    if c.dtype != want or c.numel() != n ** dim:
+        raise ValueError(f"c must be {want} with n^dim values")
+    g = pr_grid(dim, (ctypes.c_int64 * 3)(*([n] * dim + [0] * (3 - dim))), ratio)
+    o = pr_options(dtype, grad_order, 0, tol, block_depth, 0)
+    out = ctypes.c_void_p()
+    st = lib.pr_create(ctypes.byref(g), ctypes.c_void_p(c.data_ptr()), dt_f, dt_c, N, T,
+                       ctypes.byref(o), ctypes.byref(out))
+    _check(st, None)
+    return Context(out.value, dim, n, N, dtype)
+
+
+def pr_fine_all_slices(ctx: Context, u_in, v_in, u_out, v_out, n_begin: int = 0,
+                       n_end: Optional[int] = None, stream=None) -> None:
+    n_end = ctx.N if n_end is None else n_end
+    st = load().pr_fine_all_slices(ctx.handle, ctx._arr(u_in, "u_in"), ctx._arr(v_in, "v_in"),
+                                   ctx._arr(u_out, "u_out"), ctx._arr(v_out, "v_out"),
+                                   n_begin, n_end, ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, ctx.handle)
+
+
+def pr_check(ctx: Context, stream=None) -> None:
+    _check(load().pr_check(ctx.handle, ctypes.c_void_p(_stream_ptr(stream))), ctx.handle)
+
+
+def pr_info(ctx: Context) -> dict:
+    mf, mc, bd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    pts = ctypes.c_int64()
+    _check(load().pr_info(ctx.handle, ctypes.byref(mf), ctypes.byref(mc), ctypes.byref(pts),
+                          ctypes.byref(bd)), ctx.handle)
+    return {"m_f": mf.value, "m_c": mc.value, "pts": pts.value, "block_depth": bd.value}
+
+
+def pr_energy(ctx: Context, u, v, n_begin: int = 0, n_end: Optional[int] = None,
+              stream=None) -> list[float]:
+    n_end = ctx.N if n_end is None else n_end
+    out = (ctypes.c_double * max(1, n_end - n_begin))()
+    st = load().pr_energy(ctx.handle, ctx._arr(u, "u"), ctx._arr(v, "v"), n_begin, n_end, out,
+                          ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, ctx.handle)
+    return list(out)[: n_end - n_begin]
+
+
+def pr_profile(ctx: Context, on: bool) -> None:
+    _check(load().pr_profile(ctx.handle, 1 if on else 0), ctx.handle)
+
+
+def pr_profile_read(ctx: Context, kind: int) -> tuple[int, float]:
+    """(launches, summed milliseconds) of kernel kind 0 (fused pass) or 1 (single level)."""
+    cnt, ms = ctypes.c_int(), ctypes.c_double()
+    _check(load().pr_profile_read(ctx.handle, kind, ctypes.byref(cnt), ctypes.byref(ms)),
+           ctx.handle)
+    return cnt.value, ms.value

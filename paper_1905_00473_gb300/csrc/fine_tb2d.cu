@@ -1,0 +1,411 @@
+// 2D FP32 fine propagator with temporal blocking: B velocity-Verlet levels
+// per HBM pass, all slices of a sweep in one persistent launch.
+//
+// What is computed is exactly the level recurrence of fine_naive.cu (kick
+// v += w_g kappa D(u), drift u += dt v, Sec. 3.1 scheme, Alg. 3 parFor over
+// slices); this file only changes where the data lives while it is computed.
+//
+// Geometry.  A CTA owns full rows of one slice (periodic in x inside the
+// CTA, so there is no x-halo): thread t holds columns 4t..4t+3 of every row
+// in registers.  Rows stream through a B-deep software pipeline: at
+// iteration i the row i arrives, level l (l = 0..B-1) advances row i-1-l by
+// one kick+drift, and row i-B leaves the pipeline finished.  A level needs
+// its own column's rows above/below (registers) and the x-neighbours of its
+// edge columns, which come from the neighbouring threads through a small
+// double-buffered shared array written by the level below one iteration
+// earlier.  One __syncthreads per row.
+//
+// Loads.  One elected thread streams rows with cp.async.bulk (TMA bulk
+// copies: rows are contiguous and 16-byte aligned) into a shared-memory ring
+// guarded by one mbarrier per slot.  Waits are bounded: after ~2 s the CTA
+// records PR_ETIMEOUT in a device flag and leaves its loop.
+//
+// Precision.  Between passes u is (u_hi float, residual byte); inside a pass
+// the state is du = u - u_hi with the stencil applied as
+// D(u) = D0 + D(du), D0 = D(u_hi) formed from differences once per pass.
+//
+// Work split.  The N*n rows of the batch are cut into one contiguous range
+// per CTA (persistent grid of #SM * occupancy CTAs); a range that crosses a
+// slice boundary is processed as separate segments, each with its own
+// L-row halo above and below (periodic in y).
+#include "pr_internal.cuh"
+
+namespace {
+
+constexpr int kCpt = 4;      // columns per thread
+constexpr int kPrefetch = 2; // rows in flight ahead of the consumer
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: false after `limit_ns` without completion
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                         uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+struct Tb2dParams {
+    const float* u_in;
+    const float* v_in;
+    const int8_t* r_in;   // null: zero residual (first pass)
+    const float* kap;
+    float* u_out;
+    float* v_out;
+    int8_t* r_out;        // null: last pass, residual folded into u
+    int* flag;
+    int64_t rows_total;   // nslices * n
+    int n;
+    int g0, levels, m;
+    float dt;
+};
+
+template <int NT, int B>
+struct Smem {
+    static constexpr int W = NT * kCpt;        // row width = n
+    static constexpr int RD = B + kPrefetch + 2;  // deep ring: u0, kappa, D0
+    static constexpr int RS = kPrefetch + 2;      // shallow ring: v, residual
+    static constexpr size_t deep_bytes = (size_t)RD * 3 * W * 4;
+    static constexpr size_t shallow_bytes = (size_t)RS * (W * 4 + W);
+    static constexpr size_t xbuf_bytes = (size_t)2 * (B + 1) * 2 * NT * 4;
+    static constexpr size_t bar_bytes = (size_t)RD * 8;
+    static constexpr size_t total = deep_bytes + shallow_bytes + xbuf_bytes + bar_bytes;
+};
+
+template <int NT, int B>
+__global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
+    using S = Smem<NT, B>;
+    constexpr int W = S::W;
+    constexpr int RD = S::RD;
+    constexpr int RS = S::RS;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* deep = (float*)smem;                                        // [RD][3][W]
+    unsigned char* shallow = smem + S::deep_bytes;                     // [RS][W*4 + W]
+    float* xbuf = (float*)(smem + S::deep_bytes + S::shallow_bytes);   // [2][B+1][2][NT]
+    uint64_t* bars = (uint64_t*)(smem + S::deep_bytes + S::shallow_bytes + S::xbuf_bytes);
+
+    const int t = threadIdx.x;
+    const int n = p.n;
+    const int64_t pts = (int64_t)n * n;
+    const int L = p.levels;
+
+    if (t == 0) {
+        for (int s = 0; s < RD; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    uint64_t pol_stream = 0, pol_keep = 0;
+    if (t == 0) {
+        pol_stream = policy_evict_first();
+        pol_keep = policy_evict_last();
+    }
+    const uint32_t row_bytes = (uint32_t)W * 4;
+    const uint32_t tx_bytes = 3 * row_bytes + (p.r_in ? (uint32_t)W : 0u);
+
+    // persistent contiguous row range of this CTA
+    const int64_t r_begin = p.rows_total * blockIdx.x / gridDim.x;
+    const int64_t r_end = p.rows_total * (blockIdx.x + 1) / gridDim.x;
+
+    uint32_t issued = 0;    // running count of ring rows issued by this CTA
+    uint32_t consumed = 0;  // running count of ring rows waited for
+    uint32_t it_par = 0;    // running iteration parity for xbuf
+
+    // kick weight and drift flag of level l (uniform)
+    auto kick_w = [&](int l) { const int g = p.g0 + l; return (g == 0 || g == p.m) ? 0.5f : 1.0f; };
+    auto drifts = [&](int l) { return (p.g0 + l) < p.m; };
+
+    bool aborted = false;
+    int timed_out = 0;      // this thread's bounded wait gave up
+    for (int64_t seg0 = r_begin; seg0 < r_end && !aborted;) {
+        const int64_t slice = seg0 / n;
+        const int ya = (int)(seg0 - slice * n);
+        const int64_t seg1 = min(r_end, (slice + 1) * (int64_t)n);
+        const int H = (int)(seg1 - seg0);
+        seg0 = seg1;
+        const int nload = H + 2 * L;          // rows loaded: local 0..nload-1
+        const int niter = H + L + B;          // iterations of the pipeline
+        const float* u_s = p.u_in + slice * pts;
+        const float* v_s = p.v_in + slice * pts;
+        const int8_t* r_s = p.r_in ? p.r_in + slice * pts : nullptr;
+        const uint32_t base = issued;         // ring index of local row 0
+        auto gy = [&](int rho) { int y = ya - L + rho; y %= n; return y < 0 ? y + n : y; };
+
+        auto issue = [&](int rho) {
+            const uint32_t q = base + (uint32_t)rho;
+            const int sd = (int)(q % RD), ss = (int)(q % RS);
+            const int64_t off = (int64_t)gy(rho) * n;
+            uint64_t* bar = &bars[sd];
+            mbar_expect_tx(bar, tx_bytes);
+            float* drow = deep + (size_t)sd * 3 * W;
+            unsigned char* srow = shallow + (size_t)ss * (W * 4 + W);
+            bulk_g2s(drow, u_s + off, row_bytes, bar, pol_stream);
+            bulk_g2s(drow + W, p.kap + off, row_bytes, bar, pol_keep);
+            bulk_g2s(srow, v_s + off, row_bytes, bar, pol_stream);
+            if (r_s) bulk_g2s(srow + W * 4, r_s + off, (uint32_t)W, bar, pol_stream);
+        };
+        if (t == 0) {
+            for (int rho = 0; rho < kPrefetch && rho < nload; ++rho) issue(rho);
+        }
+        issued += (uint32_t)nload;
+
+        // pipeline registers: du of level l at the two rows below its next row
+        float P1[B][kCpt], P2[B][kCpt], V[B + 1][kCpt];
+#pragma unroll
+        for (int l = 0; l < B; ++l)
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) P1[l][k] = P2[l][k] = 0.0f;
+#pragma unroll
+        for (int l = 0; l <= B; ++l)
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) V[l][k] = 0.0f;
+
+        for (int i = 0; i < niter; ++i) {
+            if (t == 0 && i + kPrefetch < nload) issue(i + kPrefetch);
+            const uint32_t par = it_par & 1u;
+            float* xw = xbuf + (size_t)par * (B + 1) * 2 * NT;         // written this iteration
+            const float* xr = xbuf + (size_t)(par ^ 1u) * (B + 1) * 2 * NT;  // written last iteration
+
+            float fresh[B + 1][kCpt];
+            // ---- load stage: row i arrives -------------------------------
+            if (i < nload) {
+                const uint32_t q = base + (uint32_t)i;
+                const int sd = (int)(q % RD), ss = (int)(q % RS);
+                if (!timed_out && !mbar_wait_bounded(&bars[sd], (q / RD) & 1u, 2000000000ull)) {
+                    atomicExch(p.flag, 1);
+                    timed_out = 1;
+                }
+                consumed = q + 1;
+                const float* drow = deep + (size_t)sd * 3 * W;
+                const unsigned char* srow = shallow + (size_t)ss * (W * 4 + W);
+                const float4 u4 = *(const float4*)(drow + kCpt * t);
+                const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
+                if (r_s) {
+                    const char4 r4 = *(const char4*)(srow + W * 4 + kCpt * t);
+                    const int8_t rr[4] = {(int8_t)r4.x, (int8_t)r4.y, (int8_t)r4.z, (int8_t)r4.w};
+#pragma unroll
+                    for (int k = 0; k < kCpt; ++k) fresh[0][k] = pr_resid_decode(rr[k], uu[k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kCpt; ++k) fresh[0][k] = 0.0f;
+                }
+                xw[0 * 2 * NT + 0 * NT + t] = fresh[0][0];
+                xw[0 * 2 * NT + 1 * NT + t] = fresh[0][kCpt - 1];
+                // D0 of row i-1 from u_hi rows i-2, i-1, i (differences)
+                if (i >= 1) {
+                    const uint32_t q1 = q - 1, q2 = (i >= 2) ? q - 2 : q - 1;
+                    float* r1 = deep + (size_t)(q1 % RD) * 3 * W;
+                    const float* r2 = deep + (size_t)(q2 % RD) * 3 * W;
+                    const float4 a = *(const float4*)(r1 + kCpt * t);
+                    const float4 b2 = *(const float4*)(r2 + kCpt * t);
+                    const float c[4] = {a.x, a.y, a.z, a.w};
+                    const float s2[4] = {b2.x, b2.y, b2.z, b2.w};
+                    const float xl = r1[(kCpt * t + W - 1) % W];
+                    const float xrr = r1[(kCpt * t + kCpt) % W];
+                    float d0[4];
+#pragma unroll
+                    for (int k = 0; k < kCpt; ++k) {
+                        const float left = k == 0 ? xl : c[k - 1];
+                        const float right = k == kCpt - 1 ? xrr : c[k + 1];
+                        d0[k] = ((left - c[k]) + (right - c[k])) + ((s2[k] - c[k]) + (uu[k] - c[k]));
+                    }
+                    *(float4*)(r1 + 2 * W + kCpt * t) = make_float4(d0[0], d0[1], d0[2], d0[3]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kCpt; ++k) fresh[0][k] = 0.0f;
+            }
+
+            // ---- levels ---------------------------------------------------
+            float VN[B + 1][kCpt];
+#pragma unroll
+            for (int l = 0; l < B; ++l) {
+                const uint32_t qrow = base + (uint32_t)(i - 1 - l);   // this level's row
+                const float* drow = deep + (size_t)(qrow % RD) * 3 * W;
+                float vin[kCpt];
+                if (l == 0) {
+                    const float4 v4 = *(const float4*)(shallow + (size_t)(qrow % RS) * (W * 4 + W) +
+                                                       (size_t)kCpt * t * 4);
+                    vin[0] = v4.x; vin[1] = v4.y; vin[2] = v4.z; vin[3] = v4.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kCpt; ++k) vin[k] = V[l][k];
+                }
+                if (l < L) {
+                    const float4 k4 = *(const float4*)(drow + W + kCpt * t);
+                    const float4 d4 = *(const float4*)(drow + 2 * W + kCpt * t);
+                    const float kk[4] = {k4.x, k4.y, k4.z, k4.w};
+                    const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
+                    const float xl = xr[l * 2 * NT + 1 * NT + (t + NT - 1) % NT];
+                    const float xrt = xr[l * 2 * NT + 0 * NT + (t + 1) % NT];
+                    const float w = kick_w(l);
+                    const bool dr = drifts(l);
+#pragma unroll
+                    for (int k = 0; k < kCpt; ++k) {
+                        const float left = k == 0 ? xl : P1[l][k - 1];
+                        const float right = k == kCpt - 1 ? xrt : P1[l][k + 1];
+                        const float sum = (left + right) + (P2[l][k] + fresh[l][k]);
+                        const float lap = dd[k] + fmaf(-4.0f, P1[l][k], sum);
+                        const float vn = fmaf(w * kk[k], lap, vin[k]);
+                        VN[l + 1][k] = vn;
+                        fresh[l + 1][k] = dr ? fmaf(p.dt, vn, P1[l][k]) : P1[l][k];
+                    }
+                    if (l + 1 < L) {
+                        xw[(l + 1) * 2 * NT + 0 * NT + t] = fresh[l + 1][0];
+                        xw[(l + 1) * 2 * NT + 1 * NT + t] = fresh[l + 1][kCpt - 1];
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kCpt; ++k) {
+                        VN[l + 1][k] = vin[k];
+                        fresh[l + 1][k] = P1[l][k];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kCpt; ++k) {
+                    P2[l][k] = P1[l][k];
+                    P1[l][k] = fresh[l][k];
+                }
+            }
+
+            // ---- row i-B leaves the pipeline ------------------------------
+            const int rho_out = i - B;
+            if (rho_out >= L && rho_out < L + H) {
+                const uint32_t qo = base + (uint32_t)rho_out;
+                const float* drow = deep + (size_t)(qo % RD) * 3 * W;
+                const float4 u4 = *(const float4*)(drow + kCpt * t);
+                const float u0[4] = {u4.x, u4.y, u4.z, u4.w};
+                const int64_t off = slice * pts + (int64_t)gy(rho_out) * n + kCpt * t;
+                float uo[4];
+                if (p.r_out) {
+                    int8_t qq[4];
+#pragma unroll
+                    for (int k = 0; k < kCpt; ++k) uo[k] = pr_sum_encode(u0[k], fresh[B][k], &qq[k]);
+                    *(char4*)(p.r_out + off) = make_char4(qq[0], qq[1], qq[2], qq[3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kCpt; ++k) uo[k] = u0[k] + fresh[B][k];
+                }
+                *(float4*)(p.u_out + off) = make_float4(uo[0], uo[1], uo[2], uo[3]);
+                *(float4*)(p.v_out + off) = make_float4(VN[B][0], VN[B][1], VN[B][2], VN[B][3]);
+            }
+#pragma unroll
+            for (int l = 1; l <= B; ++l)
+#pragma unroll
+                for (int k = 0; k < kCpt; ++k) V[l][k] = VN[l][k];
+            ++it_par;
+            // one barrier per row; it also makes the abort decision uniform
+            if (__syncthreads_or(timed_out)) { aborted = true; break; }
+        }
+    }
+    if (aborted && t == 0) {
+        // let copies still in flight land before the CTA's shared memory is released
+        for (uint32_t q = consumed; q < issued; ++q) {
+            (void)mbar_wait_bounded(&bars[q % RD], (q / RD) & 1u, 100000000ull);
+        }
+    }
+}
+
+template <int NT, int B>
+pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
+    using S = Smem<NT, B>;
+    auto kern = fine_tb2d_kernel<NT, B>;
+    static int configured_dev = -1;
+    static int blocks_per_sm = 0;
+    static int sms = 0;
+    if (configured_dev != ctx->device) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::total);
+        if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "tb2d: set shared memory size");
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, NT, S::total);
+        if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "tb2d: occupancy");
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        if (blocks_per_sm < 1) return pr_fail(ctx, PR_ECUDA, "tb2d: kernel does not fit on an SM");
+        configured_dev = ctx->device;
+    }
+    Tb2dParams p;
+    p.u_in = (const float*)ps.u_in;
+    p.v_in = (const float*)ps.v_in;
+    p.r_in = ps.r_in;
+    p.kap = (const float*)ctx->kappa;
+    p.u_out = (float*)ps.u_out;
+    p.v_out = (float*)ps.v_out;
+    p.r_out = ps.r_out;
+    p.flag = ctx->dev_flag;
+    p.rows_total = (int64_t)ps.nslices * ctx->n;
+    p.n = (int)ctx->n;
+    p.g0 = ps.g0;
+    p.levels = ps.levels;
+    p.m = ps.m;
+    p.dt = (float)ctx->dt_f;
+    int64_t grid = (int64_t)sms * blocks_per_sm;
+    if (grid > p.rows_total) grid = p.rows_total;
+    kern<<<(int)grid, NT, S::total, st>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "tb2d: launch");
+    return PR_OK;
+}
+
+constexpr int kDepth = 8;
+
+}  // namespace
+
+bool pr_tb2d_supported(const pr_ctx* ctx, int depth) {
+    if (ctx->dim != 2 || ctx->dtype != PR_F32 || depth != kDepth) return false;
+    return ctx->n == 256 || ctx->n == 512 || ctx->n == 1024;
+}
+
+pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
+    if (ps.levels == 1) return pr_launch_fine_naive(ctx, ps, st);
+    if (ps.levels < 1 || ps.levels > kDepth) return pr_fail(ctx, PR_EINVAL, "tb2d: bad level count");
+    switch (ctx->n) {
+        case 256: return launch_cfg<64, kDepth>(ctx, ps, st);
+        case 512: return launch_cfg<128, kDepth>(ctx, ps, st);
+        case 1024: return launch_cfg<256, kDepth>(ctx, ps, st);
+        default: return pr_fail(ctx, PR_EINVAL, "tb2d: unsupported grid size");
+    }
+}

@@ -1,0 +1,104 @@
+// Internal declarations of the pr library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pr.h"
+
+struct pr_ctx {
+    int device = 0;
+    int dim = 0;
+    int64_t n = 0;            // fine points per axis
+    int64_t pts = 0;          // n^dim
+    int ratio = 1;
+    int N = 0;                // slices
+    int dtype = PR_F32;
+    double T = 0, dt_com = 0, dt_f = 0, dt_c = 0, dx = 0;
+    int m_f = 0, m_c = 0;
+    int block_depth = 1;      // fine steps (kicks) per HBM pass
+    double cmax = 0;
+    void* kappa = nullptr;    // dtype, c^2 dt_f / dx^2
+    double* cinv2 = nullptr;  // FP64 c^-2 (energy weights)
+    // ping-pong state between passes, [N][pts] each: u, v (dtype), r (int8)
+    void* su[2] = {nullptr, nullptr};
+    void* sv[2] = {nullptr, nullptr};
+    int8_t* sr[2] = {nullptr, nullptr};
+    double* partials = nullptr;     // energy partial sums
+    int64_t partials_len = 0;
+    int* dev_flag = nullptr;        // device-side error flag (bounded waits)
+    std::string err;
+    // pr_profile: event pairs around launches, by kernel kind
+    bool prof_on = false;
+    struct ProfRec { int kind; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+};
+
+// ---- status helpers --------------------------------------------------------
+pr_status pr_fail(pr_ctx* ctx, pr_status st, const std::string& msg);
+pr_status pr_cuda_fail(pr_ctx* ctx, cudaError_t e, const char* what);
+
+#define PR_CUDA_TRY(ctx, call)                                   \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return pr_cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// ---- the rounding-residual byte -------------------------------------------
+// Between HBM passes the FP32 displacement is stored as u_hi (float) plus a
+// signed byte q carrying the rounding residual r = (u0 + du) - u_hi in units
+// of ulp(u_hi)/256 (|r| <= ulp/2, so |q| <= 128, clamped to 127).  The scale
+// is a power of two taken from u_hi's exponent field, so encode and decode
+// are exact apart from the final rounding of q; |u_hi| < 2^-95 drops the
+// residual.
+__device__ __forceinline__ float pr_resid_scale(float uhi) {
+    uint32_t e = __float_as_uint(uhi) & 0x7f800000u;
+    return (e > (31u << 23)) ? __uint_as_float(e - (31u << 23)) : 0.0f;
+}
+__device__ __forceinline__ float pr_resid_inv_scale(float uhi) {
+    uint32_t e = (__float_as_uint(uhi) & 0x7f800000u) >> 23;
+    return (e > 31u) ? __uint_as_float((285u - e) << 23) : 0.0f;
+}
+__device__ __forceinline__ float pr_resid_decode(int8_t q, float uhi) {
+    return (float)q * pr_resid_scale(uhi);
+}
+// Round u0 + du to float and encode the rounding error (TwoSum, Knuth).
+__device__ __forceinline__ float pr_sum_encode(float u0, float du, int8_t* q) {
+    float s = __fadd_rn(u0, du);
+    float bb = __fsub_rn(s, u0);
+    float r = __fadd_rn(__fsub_rn(u0, __fsub_rn(s, bb)), __fsub_rn(du, bb));
+    float t = rintf(r * pr_resid_inv_scale(s));
+    t = fminf(fmaxf(t, -127.0f), 127.0f);
+    *q = (int8_t)(int)t;
+    return s;
+}
+
+// ---- kernels launched by the API -------------------------------------------
+struct pr_pass {
+    // state in: u (dtype), v (dtype), r (int8 or null = zero residual)
+    const void* u_in;
+    const void* v_in;
+    const int8_t* r_in;
+    // state out: r_out null on the last pass (residual folded into u)
+    void* u_out;
+    void* v_out;
+    int8_t* r_out;
+    int nslices;          // slices in this launch (pointers already offset)
+    int g0;               // global kick index of the first level
+    int levels;           // kicks in this pass
+    int m;                // steps per slice (kick m is the final half kick)
+};
+
+// one kick(+drift) per launch, any dim/dtype (the reference path of the library)
+pr_status pr_launch_fine_naive(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
+// 2D FP32 temporally blocked streaming kernel; returns PR_EINVAL if the
+// geometry is not supported (caller falls back to the naive path)
+bool pr_tb2d_supported(const pr_ctx* ctx, int depth);
+pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
+pr_status pr_launch_energy(pr_ctx* ctx, const void* u, const void* v, int nslices,
+                           double* e_host, cudaStream_t st);

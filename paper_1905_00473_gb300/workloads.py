@@ -114,6 +114,7 @@ class Workload:
     tol: float = 1e-13
     grad_order: int = 4
     seed: int = 19050473
+    m_f_fixed: Optional[int] = None  # overrides the time-step rule (test cases)
 
     @property
     def n_coarse(self) -> int:
@@ -141,10 +142,14 @@ class Workload:
 
     @property
     def m_f(self) -> int:
+        if self.m_f_fixed is not None:
+            return self.m_f_fixed
         return step_counts(self.dt_com, self.dx_f, self.cmax)[0]
 
     @property
     def m_c(self) -> int:
+        if self.m_f_fixed is not None:
+            return max(1, -(-self.m_f_fixed // 4))
         return step_counts(self.dt_com, self.dx_f, self.cmax)[1]
 
     @property
@@ -286,3 +291,27 @@ def slice_states(w: Workload, n_slices: Optional[int] = None, seed: int = 0,
             amp = rng.uniform(0.25, 1.0) * rng.choice([-1.0, 1.0])
             v[s] += amp * (w.cmax / wid) * periodic_gaussian(w.dim, w.n_fine, cen, wid)
     return w.cast(u), w.cast(v)
+
+
+def custom_case(dim: int, n: int, n_slices: int, m_f: int, dtype: str = "f32",
+                medium: str = "smooth", seed: int = 5) -> Workload:
+    """A small problem with a prescribed step count m_f at CFL 0.25/max c.
+
+    medium: "smooth" (8 random modes, c in [1, 2]) or "inclusion"
+    (c = 3 on [0.3,0.7]^dim, else 1).
+    """
+    rng = np.random.default_rng(seed)
+    if medium == "inclusion":
+        coords = node_coords(dim, n)
+        inside = np.ones([n] * dim, dtype=bool)
+        for x in coords:
+            inside = inside & (x >= 0.3) & (x <= 0.7)
+        c = np.where(inside, 3.0, 1.0)
+    else:
+        c = smooth_random_speed(dim, n, rng)
+    w = Workload(f"{dim}d-{n}-N{n_slices}-m{m_f}-{medium}-{dtype}", dim, n, 4, n_slices, 1.0,
+                 dtype, c, np.zeros([n] * dim), np.zeros([n] * dim), seed=seed, m_f_fixed=m_f)
+    w.c = w.cast(w.c)
+    dt_f = 0.25 * w.dx_f / w.cmax
+    w.t_final = n_slices * m_f * dt_f
+    return w

@@ -1,0 +1,51 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+entry point declared in include/pr.h.  No compute call is made here."""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+from paper_1905_00473_gb300 import binding
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1905_00473_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = binding.declared_symbols()
+    for must in ("pr_create", "pr_destroy", "pr_fine_all_slices", "pr_last_error", "pr_check",
+                 "pr_info", "pr_energy"):
+        assert must in names, must
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in binding.declared_symbols():
+        assert hasattr(lib, name), f"{name} declared in pr.h but not exported"
+    nm = shutil.which("nm")
+    if nm:
+        out = subprocess.run([nm, "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+        exported = set(re.findall(r"\bT (pr_\w+)", out))
+        assert set(binding.declared_symbols()) <= exported
+
+
+def test_binding_signatures_cover_the_header(libpath):
+    assert set(binding.declared_symbols()) <= set(binding._SIGNATURES)
+
+
+def test_null_arguments_are_rejected_without_a_device(libpath):
+    lib = binding.load(libpath)
+    out = ctypes.c_void_p()
+    st = lib.pr_create(None, None, 1e-3, 4e-3, 8, 1.0, None, ctypes.byref(out))
+    assert st == 1 and out.value is None
+    assert b"NULL" in lib.pr_last_error(None)
+    assert lib.pr_fine_all_slices(None, None, None, None, None, 0, 1, None) == 1
+    lib.pr_destroy(None)

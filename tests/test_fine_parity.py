@@ -1,0 +1,192 @@
+"""GPU parity of pr_fine_all_slices (F over all slices, Alg. 3 parFor; Sec. 3.1
+scheme) against the FP64 oracle on the same seeded inputs.
+
+Bar: relative energy-norm error per slice <= 1e-5 in FP32 (north-star
+tolerance) and <= 1e-11 in FP64; the relative l2 error of u is checked too.
+Small cases span several passes of the fused kernel, a ragged last pass and
+the slice-crossing row ranges of its persistent work split; the full-size
+configurations are checked on sampled slices against the oracle and on every
+slice through the exactly conserved modified Verlet energy.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import energy
+from paper_1905_00473_gb300 import workloads as W
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_all(w, ctx, u, v, slices=None):
+    ug, vg = P.run_gpu(ctx, u, v, w.dtype)
+    slices = range(u.shape[0]) if slices is None else slices
+    worst = 0.0
+    for s in slices:
+        ur, vr = P.oracle_slice(w, u[s], v[s])
+        e, l2 = P.slice_errors(w, ug[s], vg[s], ur, vr)
+        worst = max(worst, e)
+        assert e <= P.tol_for(w), (w.name, s, e)
+        assert l2 <= P.tol_for(w), (w.name, s, l2)
+    return ug, vg, worst
+
+
+@pytest.mark.parametrize("n,m_f,N,medium", [
+    (256, 20, 3, "inclusion"),   # passes of 8, 8, 5 levels; rows split across 3 slices
+    (256, 7, 2, "smooth"),       # one full pass of 8 levels
+    (256, 1, 2, "smooth"),       # two levels: single short pass
+    (512, 16, 2, "smooth"),      # 17 levels: 8, 8, then a one-level pass
+    (1024, 12, 1, "inclusion"),  # widest tile, 13 levels
+])
+def test_fused_2d_matches_oracle(lib, n, m_f, N, medium):
+    w = W.custom_case(2, n, N, m_f, "f32", medium)
+    ctx = P.make_ctx(w)
+    from paper_1905_00473_gb300 import binding
+    assert binding.pr_info(ctx)["block_depth"] == 8
+    u, v = W.slice_states(w, seed=1)
+    _check_all(w, ctx, u, v)
+
+
+@pytest.mark.parametrize("dim,n,m_f,N,dtype", [
+    (2, 48, 9, 3, "f32"),      # grid the fused kernel does not take: one level per pass
+    (1, 64, 13, 4, "f32"),
+    (3, 16, 6, 3, "f32"),
+    (2, 40, 9, 2, "f64"),
+    (3, 12, 5, 2, "f64"),
+])
+def test_single_level_path_matches_oracle(lib, dim, n, m_f, N, dtype):
+    w = W.custom_case(dim, n, N, m_f, dtype)
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=2)
+    _check_all(w, ctx, u, v)
+
+
+def test_forced_single_level_path_on_fused_geometry(lib):
+    w = W.custom_case(2, 256, 2, 10, "f32", "inclusion")
+    ctx = P.make_ctx(w, block_depth=1)
+    from paper_1905_00473_gb300 import binding
+    assert binding.pr_info(ctx)["block_depth"] == 1
+    u, v = W.slice_states(w, seed=3)
+    _check_all(w, ctx, u, v)
+
+
+def test_config1_1d_fp64_full(lib):
+    w = W.config1()
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=4)
+    _check_all(w, ctx, u, v)
+
+
+def test_inplace_and_slice_subset(lib):
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = W.custom_case(2, 256, 4, 12, "f32", "smooth")
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=5)
+    ud = torch.tensor(u, dtype=torch.float32, device="cuda")
+    vd = torch.tensor(v, dtype=torch.float32, device="cuda")
+    u_keep, v_keep = ud.clone(), vd.clone()
+    binding.pr_fine_all_slices(ctx, ud, vd, ud, vd, 1, 3)   # in place, slices 1 and 2
+    binding.pr_check(ctx)
+    ug, vg = ud.double().cpu().numpy(), vd.double().cpu().numpy()
+    for s in (0, 3):   # untouched
+        assert torch.equal(ud[s], u_keep[s]) and torch.equal(vd[s], v_keep[s])
+    for s in (1, 2):
+        ur, vr = P.oracle_slice(w, u[s], v[s])
+        e, _ = P.slice_errors(w, ug[s], vg[s], ur, vr)
+        assert e <= P.TOL_ENERGY_F32
+    # one-pass sweep in place goes through scratch
+    w1 = W.custom_case(2, 256, 2, 3, "f32", "smooth")
+    ctx1 = P.make_ctx(w1)
+    u1, v1 = W.slice_states(w1, seed=6)
+    ug1, vg1 = P.run_gpu(ctx1, u1, v1, "f32", inplace=True)
+    for s in range(2):
+        ur, vr = P.oracle_slice(w1, u1[s], v1[s])
+        assert P.slice_errors(w1, ug1[s], vg1[s], ur, vr)[0] <= P.TOL_ENERGY_F32
+
+
+def test_empty_range_and_invalid_arguments(lib):
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = W.custom_case(2, 256, 3, 8, "f32")
+    ctx = P.make_ctx(w)
+    u = torch.zeros((3, 256, 256), device="cuda")
+    v = torch.zeros_like(u)
+    uo = torch.full_like(u, 7.0)
+    vo = torch.full_like(u, 7.0)
+    binding.pr_fine_all_slices(ctx, u, v, uo, vo, 2, 2)   # empty: no-op
+    binding.pr_check(ctx)
+    assert bool((uo == 7.0).all())
+    with pytest.raises(binding.PrError) as ei:
+        binding.pr_fine_all_slices(ctx, u, v, uo, vo, 2, 4)
+    assert ei.value.status == 1
+    with pytest.raises(binding.PrError):
+        binding.pr_fine_all_slices(ctx, u, v, v, uo)       # output overlaps input
+    big = torch.zeros(4 * 256 * 256, device="cuda")
+    with pytest.raises(binding.PrError):
+        binding.pr_fine_all_slices(ctx, big[1:1 + 3 * 65536].view(3, 256, 256), v, uo, vo)  # unaligned
+    # zero input stays exactly zero
+    binding.pr_fine_all_slices(ctx, u, v, uo, vo)
+    binding.pr_check(ctx)
+    assert not bool(uo.any()) and not bool(vo.any())
+
+
+def test_create_validates_steps_and_cfl(lib):
+    import torch
+    from paper_1905_00473_gb300 import binding
+    c = torch.ones(64 * 64, device="cuda")
+    dx = 1 / 64
+    with pytest.raises(binding.PrError):   # (T/N)/dt_f not an integer
+        binding.pr_create(2, 64, 4, c, 0.3 * dx, 1.2 * dx, 4, 4 * 10.5 * 0.3 * dx)
+    with pytest.raises(binding.PrError):   # CFL violated on the fine grid
+        binding.pr_create(2, 64, 4, c, 0.8 * dx, 0.8 * dx, 4, 4 * 0.8 * dx)
+    with pytest.raises(binding.PrError):   # c <= 0
+        binding.pr_create(2, 64, 4, c * 0, 0.2 * dx, 0.8 * dx, 4, 4 * 0.8 * dx)
+    with pytest.raises(binding.PrError):   # ratio does not divide n
+        binding.pr_create(2, 64, 5, c, 0.2 * dx, 0.8 * dx, 4, 4 * 0.8 * dx)
+    ctx = binding.pr_create(2, 64, 4, c, 0.2 * dx, 0.8 * dx, 4, 4 * 0.8 * dx)
+    assert binding.pr_info(ctx)["m_f"] == 4 and binding.pr_info(ctx)["m_c"] == 1
+
+
+def test_energy_matches_oracle(lib):
+    import torch
+    from paper_1905_00473_gb300 import binding
+    for w in (W.custom_case(2, 256, 3, 4, "f32", "inclusion"), W.custom_case(1, 64, 2, 4, "f64"),
+              W.custom_case(3, 16, 2, 4, "f32")):
+        ctx = P.make_ctx(w)
+        u, v = W.slice_states(w, seed=7)
+        dt = torch.float32 if w.dtype == "f32" else torch.float64
+        e = binding.pr_energy(ctx, torch.tensor(u, dtype=dt, device="cuda"),
+                              torch.tensor(v, dtype=dt, device="cuda"))
+        for s in range(w.n_slices):
+            ref = energy.discrete_wave_energy(u[s], v[s], w.c, w.dx_f, order=4)
+            assert abs(e[s] - ref) <= 1e-12 * ref, (w.name, s, e[s], ref)
+
+
+def _modified_energy(u, v, c, dt, dx):
+    fwd = [(np.roll(u, -1, axis=ax) - u) / dx for ax in range(u.ndim)]
+    lap = sum((g - np.roll(g, 1, axis=ax)) / dx for ax, g in enumerate(fwd))
+    a = c * c * lap
+    return ((0.5 * np.sum(v * v / (c * c)) + 0.5 * sum(np.sum(g * g) for g in fwd)
+             - dt * dt / 8.0 * np.sum(a * a / (c * c))) * dx ** u.ndim)
+
+
+@pytest.mark.parametrize("cfg", ["2", "3"])
+def test_full_size_configs(lib, cfg):
+    """Full configuration, all slices in the bench's launch configuration:
+    the oracle on two sampled slices, the conserved modified energy on all."""
+    w = W.CONFIGS[cfg]()
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=0)
+    ug, vg = P.run_gpu(ctx, u, v, w.dtype)
+    rng = np.random.default_rng(int(cfg))
+    for s in sorted(rng.choice(w.n_slices, size=2, replace=False)):
+        ur, vr = P.oracle_slice(w, u[s], v[s])
+        e, l2 = P.slice_errors(w, ug[s], vg[s], ur, vr)
+        assert e <= P.TOL_ENERGY_F32 and l2 <= P.TOL_ENERGY_F32, (cfg, s, e, l2)
+    for s in range(w.n_slices):
+        h0 = _modified_energy(u[s], v[s], w.c, w.dt_f, w.dx_f)
+        h1 = _modified_energy(ug[s], vg[s], w.c, w.dt_f, w.dx_f)
+        assert math.isfinite(h1) and abs(h1 - h0) <= 2e-5 * abs(h0), (cfg, s, h0, h1)
