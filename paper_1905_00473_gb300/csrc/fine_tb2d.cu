@@ -13,12 +13,15 @@
 // its own column's rows above/below (registers) and the x-neighbours of its
 // edge columns, which come from the neighbouring threads through a small
 // double-buffered shared array written by the level below one iteration
-// earlier.  One __syncthreads per row.
+// earlier.  One barrier per row.
 //
 // Loads.  One elected thread streams rows with cp.async.bulk (TMA bulk
-// copies: rows are contiguous and 16-byte aligned) into a shared-memory ring
-// guarded by one mbarrier per slot.  Waits are bounded: after ~2 s the CTA
-// records PR_ETIMEOUT in a device flag and leaves its loop.
+// copies: rows are contiguous and 16-byte aligned) into shared-memory rings
+// guarded by one mbarrier per row slot: kappa into a 16-row ring that also
+// holds D0 (below) for the rows in flight, u_hi, u_t and the residual byte
+// into a 5-row ring.  The finished row re-reads its u_hi from L2.  Waits are
+// bounded: after ~2 s the CTA records PR_ETIMEOUT in a device flag and all
+// its threads leave the loop together.
 //
 // Precision.  Between passes u is (u_hi float, residual byte); inside a pass
 // the state is du = u - u_hi with the stencil applied as
@@ -28,12 +31,20 @@
 // per CTA (persistent grid of #SM * occupancy CTAs); a range that crosses a
 // slice boundary is processed as separate segments, each with its own
 // L-row halo above and below (periodic in y).
+//
+// Variants.  MID = a pass strictly inside the sweep (no half kick, every
+// level drifts, all B levels active), which is nearly every pass; the
+// general variant handles the first pass (half kick at g = 0), the last pass
+// (half kick at g = m, no drift, fewer than B levels: the missing levels pass
+// rows through unchanged).
 #include "pr_internal.cuh"
 
 namespace {
 
-constexpr int kCpt = 4;      // columns per thread
-constexpr int kPrefetch = 2; // rows in flight ahead of the consumer
+constexpr int kCpt = 4;       // columns per thread
+constexpr int kPrefetch = 2;  // rows in flight ahead of the consumer
+constexpr int kRD = 16;       // kappa/D0 ring (power of two)
+constexpr int kRS = 5;        // u_hi, u_t, residual ring
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -78,14 +89,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
-__device__ __forceinline__ uint64_t policy_evict_first() {
+__device__ __forceinline__ uint64_t policy(int kind) {
     uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    if (kind == 0) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    else if (kind == 1) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 
@@ -106,95 +114,90 @@ struct Tb2dParams {
 
 template <int NT, int B>
 struct Smem {
-    static constexpr int W = NT * kCpt;        // row width = n
-    static constexpr int RD = B + kPrefetch + 2;  // deep ring: u0, kappa, D0
-    static constexpr int RS = kPrefetch + 2;      // shallow ring: v, residual
-    static constexpr size_t deep_bytes = (size_t)RD * 3 * W * 4;
-    static constexpr size_t shallow_bytes = (size_t)RS * (W * 4 + W);
+    static constexpr int W = NT * kCpt;                       // row width = n
+    static constexpr size_t deep_row = (size_t)2 * W * 4;      // kappa, D0
+    static constexpr size_t sh_row = (size_t)W * 4 * 2 + W;    // u_hi, u_t, residual
+    static constexpr size_t deep_bytes = kRD * deep_row;
+    static constexpr size_t sh_bytes = kRS * sh_row;
     static constexpr size_t xbuf_bytes = (size_t)2 * (B + 1) * 2 * NT * 4;
-    static constexpr size_t bar_bytes = (size_t)RD * 8;
-    static constexpr size_t total = deep_bytes + shallow_bytes + xbuf_bytes + bar_bytes;
+    static constexpr size_t bar_bytes = (size_t)kRD * 8;
+    static constexpr size_t total = deep_bytes + sh_bytes + xbuf_bytes + bar_bytes;
 };
 
-template <int NT, int B>
+template <int NT, int B, bool MID>
 __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     using S = Smem<NT, B>;
     constexpr int W = S::W;
-    constexpr int RD = S::RD;
-    constexpr int RS = S::RS;
     extern __shared__ __align__(128) unsigned char smem[];
-    float* deep = (float*)smem;                                        // [RD][3][W]
-    unsigned char* shallow = smem + S::deep_bytes;                     // [RS][W*4 + W]
-    float* xbuf = (float*)(smem + S::deep_bytes + S::shallow_bytes);   // [2][B+1][2][NT]
-    uint64_t* bars = (uint64_t*)(smem + S::deep_bytes + S::shallow_bytes + S::xbuf_bytes);
+    unsigned char* deep = smem;                                            // [kRD][kappa W | D0 W]
+    unsigned char* shal = smem + S::deep_bytes;                            // [kRS][u W | v W | r W]
+    float* xbuf = (float*)(smem + S::deep_bytes + S::sh_bytes);            // [2][B+1][2][NT]
+    uint64_t* bars = (uint64_t*)(smem + S::deep_bytes + S::sh_bytes + S::xbuf_bytes);
 
     const int t = threadIdx.x;
     const int n = p.n;
     const int64_t pts = (int64_t)n * n;
-    const int L = p.levels;
+    const int L = MID ? B : p.levels;
+    const float dt = p.dt;
+    const int tl = (t + NT - 1) % NT, tr = (t + 1) % NT;
+    const int cl = (kCpt * t + W - 1) % W, cr = (kCpt * t + kCpt) % W;
 
     if (t == 0) {
-        for (int s = 0; s < RD; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < kRD; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
 
-    uint64_t pol_stream = 0, pol_keep = 0;
+    uint64_t pol_first = 0, pol_last = 0, pol_norm = 0;
     if (t == 0) {
-        pol_stream = policy_evict_first();
-        pol_keep = policy_evict_last();
+        pol_first = policy(0);
+        pol_last = policy(1);
+        pol_norm = policy(2);
     }
     const uint32_t row_bytes = (uint32_t)W * 4;
     const uint32_t tx_bytes = 3 * row_bytes + (p.r_in ? (uint32_t)W : 0u);
 
-    // persistent contiguous row range of this CTA
     const int64_t r_begin = p.rows_total * blockIdx.x / gridDim.x;
     const int64_t r_end = p.rows_total * (blockIdx.x + 1) / gridDim.x;
 
-    uint32_t issued = 0;    // running count of ring rows issued by this CTA
-    uint32_t consumed = 0;  // running count of ring rows waited for
-    uint32_t it_par = 0;    // running iteration parity for xbuf
-
-    // kick weight and drift flag of level l (uniform)
-    auto kick_w = [&](int l) { const int g = p.g0 + l; return (g == 0 || g == p.m) ? 0.5f : 1.0f; };
-    auto drifts = [&](int l) { return (p.g0 + l) < p.m; };
-
+    uint32_t issued = 0, consumed = 0, it_par = 0;
+    int timed_out = 0;
     bool aborted = false;
-    int timed_out = 0;      // this thread's bounded wait gave up
+
     for (int64_t seg0 = r_begin; seg0 < r_end && !aborted;) {
         const int64_t slice = seg0 / n;
         const int ya = (int)(seg0 - slice * n);
         const int64_t seg1 = min(r_end, (slice + 1) * (int64_t)n);
         const int H = (int)(seg1 - seg0);
         seg0 = seg1;
-        const int nload = H + 2 * L;          // rows loaded: local 0..nload-1
-        const int niter = H + L + B;          // iterations of the pipeline
+        const int nload = H + 2 * L;
+        const int niter = H + L + B;
         const float* u_s = p.u_in + slice * pts;
         const float* v_s = p.v_in + slice * pts;
         const int8_t* r_s = p.r_in ? p.r_in + slice * pts : nullptr;
-        const uint32_t base = issued;         // ring index of local row 0
-        auto gy = [&](int rho) { int y = ya - L + rho; y %= n; return y < 0 ? y + n : y; };
+        const uint32_t base = issued;
+        int ylo = ya - L;                    // global row of local row 0 (mod n)
+        ylo %= n;
+        if (ylo < 0) ylo += n;
+        auto gy = [&](int rho) { int y = ylo + rho; return y >= n ? y - n : y; };
 
         auto issue = [&](int rho) {
             const uint32_t q = base + (uint32_t)rho;
-            const int sd = (int)(q % RD), ss = (int)(q % RS);
             const int64_t off = (int64_t)gy(rho) * n;
-            uint64_t* bar = &bars[sd];
+            uint64_t* bar = &bars[q & (kRD - 1)];
+            unsigned char* drow = deep + (size_t)(q & (kRD - 1)) * S::deep_row;
+            unsigned char* srow = shal + (size_t)(q % kRS) * S::sh_row;
             mbar_expect_tx(bar, tx_bytes);
-            float* drow = deep + (size_t)sd * 3 * W;
-            unsigned char* srow = shallow + (size_t)ss * (W * 4 + W);
-            bulk_g2s(drow, u_s + off, row_bytes, bar, pol_stream);
-            bulk_g2s(drow + W, p.kap + off, row_bytes, bar, pol_keep);
-            bulk_g2s(srow, v_s + off, row_bytes, bar, pol_stream);
-            if (r_s) bulk_g2s(srow + W * 4, r_s + off, (uint32_t)W, bar, pol_stream);
+            bulk_g2s(drow, p.kap + off, row_bytes, bar, pol_last);
+            bulk_g2s(srow, u_s + off, row_bytes, bar, pol_norm);
+            bulk_g2s(srow + W * 4, v_s + off, row_bytes, bar, pol_first);
+            if (r_s) bulk_g2s(srow + W * 8, r_s + off, (uint32_t)W, bar, pol_first);
         };
-        if (t == 0) {
+        if (t == 0)
             for (int rho = 0; rho < kPrefetch && rho < nload; ++rho) issue(rho);
-        }
         issued += (uint32_t)nload;
 
-        // pipeline registers: du of level l at the two rows below its next row
         float P1[B][kCpt], P2[B][kCpt], V[B + 1][kCpt];
 #pragma unroll
         for (int l = 0; l < B; ++l)
@@ -208,25 +211,23 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         for (int i = 0; i < niter; ++i) {
             if (t == 0 && i + kPrefetch < nload) issue(i + kPrefetch);
             const uint32_t par = it_par & 1u;
-            float* xw = xbuf + (size_t)par * (B + 1) * 2 * NT;         // written this iteration
-            const float* xr = xbuf + (size_t)(par ^ 1u) * (B + 1) * 2 * NT;  // written last iteration
+            float* xw = xbuf + (size_t)par * (B + 1) * 2 * NT;
+            const float* xr = xbuf + (size_t)(par ^ 1u) * (B + 1) * 2 * NT;
+            const uint32_t q = base + (uint32_t)i;   // ring index of row i
 
             float fresh[B + 1][kCpt];
-            // ---- load stage: row i arrives -------------------------------
+            // ---- load stage: row i arrives, D0 of row i-1 -----------------
             if (i < nload) {
-                const uint32_t q = base + (uint32_t)i;
-                const int sd = (int)(q % RD), ss = (int)(q % RS);
-                if (!timed_out && !mbar_wait_bounded(&bars[sd], (q / RD) & 1u, 2000000000ull)) {
+                if (!timed_out && !mbar_wait_bounded(&bars[q & (kRD - 1)], (q / kRD) & 1u, 2000000000ull)) {
                     atomicExch(p.flag, 1);
                     timed_out = 1;
                 }
                 consumed = q + 1;
-                const float* drow = deep + (size_t)sd * 3 * W;
-                const unsigned char* srow = shallow + (size_t)ss * (W * 4 + W);
-                const float4 u4 = *(const float4*)(drow + kCpt * t);
+                const unsigned char* s0 = shal + (size_t)(q % kRS) * S::sh_row;
+                const float4 u4 = *(const float4*)(s0 + 16 * t);
                 const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
                 if (r_s) {
-                    const char4 r4 = *(const char4*)(srow + W * 4 + kCpt * t);
+                    const char4 r4 = *(const char4*)(s0 + W * 8 + kCpt * t);
                     const int8_t rr[4] = {(int8_t)r4.x, (int8_t)r4.y, (int8_t)r4.z, (int8_t)r4.w};
 #pragma unroll
                     for (int k = 0; k < kCpt; ++k) fresh[0][k] = pr_resid_decode(rr[k], uu[k]);
@@ -234,27 +235,25 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
 #pragma unroll
                     for (int k = 0; k < kCpt; ++k) fresh[0][k] = 0.0f;
                 }
-                xw[0 * 2 * NT + 0 * NT + t] = fresh[0][0];
-                xw[0 * 2 * NT + 1 * NT + t] = fresh[0][kCpt - 1];
-                // D0 of row i-1 from u_hi rows i-2, i-1, i (differences)
+                xw[t] = fresh[0][0];
+                xw[NT + t] = fresh[0][kCpt - 1];
                 if (i >= 1) {
-                    const uint32_t q1 = q - 1, q2 = (i >= 2) ? q - 2 : q - 1;
-                    float* r1 = deep + (size_t)(q1 % RD) * 3 * W;
-                    const float* r2 = deep + (size_t)(q2 % RD) * 3 * W;
-                    const float4 a = *(const float4*)(r1 + kCpt * t);
-                    const float4 b2 = *(const float4*)(r2 + kCpt * t);
+                    const float* s1 = (const float*)(shal + (size_t)((q - 1) % kRS) * S::sh_row);
+                    const float* s2 = (const float*)(shal + (size_t)((i >= 2 ? q - 2 : q - 1) % kRS) * S::sh_row);
+                    const float4 a = *(const float4*)(s1 + kCpt * t);
+                    const float4 b2 = *(const float4*)(s2 + kCpt * t);
                     const float c[4] = {a.x, a.y, a.z, a.w};
-                    const float s2[4] = {b2.x, b2.y, b2.z, b2.w};
-                    const float xl = r1[(kCpt * t + W - 1) % W];
-                    const float xrr = r1[(kCpt * t + kCpt) % W];
+                    const float s2v[4] = {b2.x, b2.y, b2.z, b2.w};
+                    const float xl = s1[cl], xrr = s1[cr];
                     float d0[4];
 #pragma unroll
                     for (int k = 0; k < kCpt; ++k) {
                         const float left = k == 0 ? xl : c[k - 1];
                         const float right = k == kCpt - 1 ? xrr : c[k + 1];
-                        d0[k] = ((left - c[k]) + (right - c[k])) + ((s2[k] - c[k]) + (uu[k] - c[k]));
+                        d0[k] = ((left - c[k]) + (right - c[k])) + ((s2v[k] - c[k]) + (uu[k] - c[k]));
                     }
-                    *(float4*)(r1 + 2 * W + kCpt * t) = make_float4(d0[0], d0[1], d0[2], d0[3]);
+                    float* dd = (float*)(deep + (size_t)((q - 1) & (kRD - 1)) * S::deep_row) + W;
+                    *(float4*)(dd + kCpt * t) = make_float4(d0[0], d0[1], d0[2], d0[3]);
                 }
             } else {
 #pragma unroll
@@ -265,39 +264,46 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
             float VN[B + 1][kCpt];
 #pragma unroll
             for (int l = 0; l < B; ++l) {
-                const uint32_t qrow = base + (uint32_t)(i - 1 - l);   // this level's row
-                const float* drow = deep + (size_t)(qrow % RD) * 3 * W;
+                const uint32_t qr = q - 1u - (uint32_t)l;   // ring index of this level's row
+                const float* drow = (const float*)(deep + (size_t)(qr & (kRD - 1)) * S::deep_row);
                 float vin[kCpt];
                 if (l == 0) {
-                    const float4 v4 = *(const float4*)(shallow + (size_t)(qrow % RS) * (W * 4 + W) +
-                                                       (size_t)kCpt * t * 4);
+                    const float4 v4 = *(const float4*)(shal + (size_t)(qr % kRS) * S::sh_row + W * 4 + 16 * t);
                     vin[0] = v4.x; vin[1] = v4.y; vin[2] = v4.z; vin[3] = v4.w;
                 } else {
 #pragma unroll
                     for (int k = 0; k < kCpt; ++k) vin[k] = V[l][k];
                 }
-                if (l < L) {
-                    const float4 k4 = *(const float4*)(drow + W + kCpt * t);
-                    const float4 d4 = *(const float4*)(drow + 2 * W + kCpt * t);
-                    const float kk[4] = {k4.x, k4.y, k4.z, k4.w};
+                if (MID || l < L) {
+                    const float4 k4 = *(const float4*)(drow + kCpt * t);
+                    const float4 d4 = *(const float4*)(drow + W + kCpt * t);
+                    float kk[4] = {k4.x, k4.y, k4.z, k4.w};
                     const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
-                    const float xl = xr[l * 2 * NT + 1 * NT + (t + NT - 1) % NT];
-                    const float xrt = xr[l * 2 * NT + 0 * NT + (t + 1) % NT];
-                    const float w = kick_w(l);
-                    const bool dr = drifts(l);
+                    const float xl = xr[l * 2 * NT + NT + tl];
+                    const float xrt = xr[l * 2 * NT + tr];
+                    bool dr = true;
+                    if (!MID) {
+                        const int g = p.g0 + l;
+                        if (g == 0 || g == p.m) {
+#pragma unroll
+                            for (int k = 0; k < kCpt; ++k) kk[k] *= 0.5f;
+                        }
+                        dr = g < p.m;
+                    }
 #pragma unroll
                     for (int k = 0; k < kCpt; ++k) {
                         const float left = k == 0 ? xl : P1[l][k - 1];
                         const float right = k == kCpt - 1 ? xrt : P1[l][k + 1];
-                        const float sum = (left + right) + (P2[l][k] + fresh[l][k]);
-                        const float lap = dd[k] + fmaf(-4.0f, P1[l][k], sum);
-                        const float vn = fmaf(w * kk[k], lap, vin[k]);
+                        // D(u) = D0 + (du_S + du_N + du_W + du_E - 4 du_C); the fresh
+                        // north row enters last to keep the level-to-level chain short
+                        const float part = dd[k] + fmaf(-4.0f, P1[l][k], (left + right) + P2[l][k]);
+                        const float vn = fmaf(kk[k], part + fresh[l][k], vin[k]);
                         VN[l + 1][k] = vn;
-                        fresh[l + 1][k] = dr ? fmaf(p.dt, vn, P1[l][k]) : P1[l][k];
+                        fresh[l + 1][k] = dr ? fmaf(dt, vn, P1[l][k]) : P1[l][k];
                     }
                     if (l + 1 < L) {
-                        xw[(l + 1) * 2 * NT + 0 * NT + t] = fresh[l + 1][0];
-                        xw[(l + 1) * 2 * NT + 1 * NT + t] = fresh[l + 1][kCpt - 1];
+                        xw[(l + 1) * 2 * NT + t] = fresh[l + 1][0];
+                        xw[(l + 1) * 2 * NT + NT + t] = fresh[l + 1][kCpt - 1];
                     }
                 } else {
 #pragma unroll
@@ -316,13 +322,11 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
             // ---- row i-B leaves the pipeline ------------------------------
             const int rho_out = i - B;
             if (rho_out >= L && rho_out < L + H) {
-                const uint32_t qo = base + (uint32_t)rho_out;
-                const float* drow = deep + (size_t)(qo % RD) * 3 * W;
-                const float4 u4 = *(const float4*)(drow + kCpt * t);
-                const float u0[4] = {u4.x, u4.y, u4.z, u4.w};
                 const int64_t off = slice * pts + (int64_t)gy(rho_out) * n + kCpt * t;
+                const float4 u4 = __ldcs((const float4*)(p.u_in + off));
+                const float u0[4] = {u4.x, u4.y, u4.z, u4.w};
                 float uo[4];
-                if (p.r_out) {
+                if (MID || p.r_out) {
                     int8_t qq[4];
 #pragma unroll
                     for (int k = 0; k < kCpt; ++k) uo[k] = pr_sum_encode(u0[k], fresh[B][k], &qq[k]);
@@ -345,16 +349,15 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     }
     if (aborted && t == 0) {
         // let copies still in flight land before the CTA's shared memory is released
-        for (uint32_t q = consumed; q < issued; ++q) {
-            (void)mbar_wait_bounded(&bars[q % RD], (q / RD) & 1u, 100000000ull);
-        }
+        for (uint32_t q = consumed; q < issued; ++q)
+            (void)mbar_wait_bounded(&bars[q & (kRD - 1)], (q / kRD) & 1u, 100000000ull);
     }
 }
 
-template <int NT, int B>
+template <int NT, int B, bool MID>
 pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     using S = Smem<NT, B>;
-    auto kern = fine_tb2d_kernel<NT, B>;
+    auto kern = fine_tb2d_kernel<NT, B, MID>;
     static int configured_dev = -1;
     static int blocks_per_sm = 0;
     static int sms = 0;
@@ -390,6 +393,12 @@ pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     return PR_OK;
 }
 
+template <int NT, int B>
+pr_status launch_depth(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
+    const bool mid = ps.levels == B && ps.g0 >= 1 && ps.g0 + B - 1 < ps.m && ps.r_in && ps.r_out;
+    return mid ? launch_cfg<NT, B, true>(ctx, ps, st) : launch_cfg<NT, B, false>(ctx, ps, st);
+}
+
 constexpr int kDepth = 8;
 
 }  // namespace
@@ -403,9 +412,9 @@ pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     if (ps.levels == 1) return pr_launch_fine_naive(ctx, ps, st);
     if (ps.levels < 1 || ps.levels > kDepth) return pr_fail(ctx, PR_EINVAL, "tb2d: bad level count");
     switch (ctx->n) {
-        case 256: return launch_cfg<64, kDepth>(ctx, ps, st);
-        case 512: return launch_cfg<128, kDepth>(ctx, ps, st);
-        case 1024: return launch_cfg<256, kDepth>(ctx, ps, st);
+        case 256: return launch_depth<64, kDepth>(ctx, ps, st);
+        case 512: return launch_depth<128, kDepth>(ctx, ps, st);
+        case 1024: return launch_depth<256, kDepth>(ctx, ps, st);
         default: return pr_fail(ctx, PR_EINVAL, "tb2d: unsupported grid size");
     }
 }

@@ -52,29 +52,26 @@ pr_status pr_cuda_fail(pr_ctx* ctx, cudaError_t e, const char* what);
 // ---- the rounding-residual byte -------------------------------------------
 // Between HBM passes the FP32 displacement is stored as u_hi (float) plus a
 // signed byte q carrying the rounding residual r = (u0 + du) - u_hi in units
-// of ulp(u_hi)/256 (|r| <= ulp/2, so |q| <= 128, clamped to 127).  The scale
-// is a power of two taken from u_hi's exponent field, so encode and decode
-// are exact apart from the final rounding of q; |u_hi| < 2^-95 drops the
-// residual.
-__device__ __forceinline__ float pr_resid_scale(float uhi) {
-    uint32_t e = __float_as_uint(uhi) & 0x7f800000u;
-    return (e > (31u << 23)) ? __uint_as_float(e - (31u << 23)) : 0.0f;
-}
-__device__ __forceinline__ float pr_resid_inv_scale(float uhi) {
-    uint32_t e = (__float_as_uint(uhi) & 0x7f800000u) >> 23;
-    return (e > 31u) ? __uint_as_float((285u - e) << 23) : 0.0f;
+// of 2^(E-31), E the exponent of u_hi, i.e. ulp(u_hi)/256 (|r| <= ulp/2, so
+// |q| <= 128; the convert saturates at [-128, 127]).  The scale is a power of
+// two built from u_hi's exponent field (clamped below at 2^-95 so that it is
+// always a normal number), so encode and decode are exact apart from the
+// rounding of q itself: the stored displacement keeps ~33 significant bits.
+__device__ __forceinline__ uint32_t pr_resid_efield(float uhi) {
+    return max(__float_as_uint(uhi) & 0x7f800000u, 32u << 23);
 }
 __device__ __forceinline__ float pr_resid_decode(int8_t q, float uhi) {
-    return (float)q * pr_resid_scale(uhi);
+    return (float)q * __uint_as_float(pr_resid_efield(uhi) - (31u << 23));
 }
 // Round u0 + du to float and encode the rounding error (TwoSum, Knuth).
 __device__ __forceinline__ float pr_sum_encode(float u0, float du, int8_t* q) {
-    float s = __fadd_rn(u0, du);
-    float bb = __fsub_rn(s, u0);
-    float r = __fadd_rn(__fsub_rn(u0, __fsub_rn(s, bb)), __fsub_rn(du, bb));
-    float t = rintf(r * pr_resid_inv_scale(s));
-    t = fminf(fmaxf(t, -127.0f), 127.0f);
-    *q = (int8_t)(int)t;
+    const float s = __fadd_rn(u0, du);
+    const float bb = __fsub_rn(s, u0);
+    const float r = __fadd_rn(__fsub_rn(u0, __fsub_rn(s, bb)), __fsub_rn(du, bb));
+    const float inv = __uint_as_float((285u << 23) - pr_resid_efield(s));  // 2^(31-E)
+    int qi;
+    asm("cvt.rni.sat.s8.f32 %0, %1;" : "=r"(qi) : "f"(__fmul_rn(r, inv)));
+    *q = (int8_t)qi;
     return s;
 }
 
