@@ -151,6 +151,47 @@ pr_status pr_profile(pr_ctx* ctx, int on);
  * of launches recorded and their summed duration in milliseconds. */
 pr_status pr_profile_read(pr_ctx* ctx, int kind, int* launches, double* total_ms);
 
+/* Size in bytes of the fixed device scratch array behind
+ * pr_fine_all_slices_noalloc (32 MiB). */
+#define PR_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* pr_fine_all_slices_noalloc -- the fine propagator over a batch of slices
+ * without any device allocation and without a context.  The paper has no
+ * counterpart: this is an interface for callers that cannot allocate device
+ * memory, so cannot use pr_create (which cudaMallocs the coefficient and
+ * scratch arrays): code running inside a framework that owns the whole device
+ * memory pool, plugins invoked from another library's stream-ordered work,
+ * real-time loops where an allocation's latency or failure is unacceptable.
+ *
+ *  dim, n       grid: n points per axis on [0,1)^dim, dim in {1,2,3}, n in [4, 2^20].
+ *  nslices      slices in the batch (0 = nothing to do).
+ *  c            DEVICE float[n^dim], wave speed at the fine nodes.
+ *  dt_f, m_f    fine step and steps per slice (m_f >= 1).  The CFL condition
+ *               max c * dt_f * sqrt(dim) * n <= 1 is the caller's to meet
+ *               (it is not checked: checking would need a device read-back).
+ *  u_in, v_in   DEVICE float[nslices][n^dim] slice states; u_out, v_out the
+ *               results, same layout; out == in allowed, other overlap is not.
+ *  stream       cudaStream_t (void*).
+ *  msg, msg_len optional caller buffer for an error message (may be NULL).
+ * Computes what pr_fine_all_slices computes for FP32 (one launch per Verlet
+ * level, the context path's single-level arithmetic).
+ *
+ * Scratch: one file-scope device array of PR_NOALLOC_SCRATCH_BYTES, held by
+ * every GPU that loads the library until the process exits.  A call needs
+ *   A(n^dim * 4) + 2 * (2 * A(nslices * n^dim * 4) + A(nslices * n^dim))
+ * bytes, A() rounding up to 256; larger requests return PR_EINVAL with the
+ * sizes in msg, before anything is launched.  No call allocates: no
+ * cudaMalloc, cudaFree or allocating library routine.  All calls share the
+ * array and it keeps the last call's contents (nothing in it needs to start at
+ * zero); calls whose GPU work overlaps race on it, so serialise them on one
+ * stream.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it: make that
+ * first call before any stream capture begins.
+ * Returns PR_OK, PR_EINVAL (arguments or size) or PR_ECUDA. */
+pr_status pr_fine_all_slices_noalloc(int dim, int64_t n, int nslices, const float* c, double dt_f,
+                                     int m_f, const float* u_in, const float* v_in, float* u_out,
+                                     float* v_out, void* stream, char* msg, size_t msg_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,9 @@ _SIGNATURES = {
                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
     "pr_energy": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_double), _P]),
+    "pr_fine_all_slices_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _P,
+                                                  ctypes.c_double, ctypes.c_int, _P, _P, _P, _P,
+                                                  _P, ctypes.c_char_p, ctypes.c_size_t]),
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double)]),
@@ -186,3 +189,29 @@ def pr_profile_read(ctx: Context, kind: int) -> tuple[int, float]:
     _check(load().pr_profile_read(ctx.handle, kind, ctypes.byref(cnt), ctypes.byref(ms)),
            ctx.handle)
     return cnt.value, ms.value
+
+
+def pr_fine_all_slices_noalloc(c, dt_f: float, m_f: int, u_in, v_in, u_out, v_out,
+                               stream=None) -> None:
+    """Context-free F over all slices with the library's fixed device scratch
+    (no device allocation); FP32 tensors, shapes [N, n, ..., n] with c [n, ..., n]."""
+    import torch
+    for name, t in (("c", c), ("u_in", u_in), ("v_in", v_in), ("u_out", u_out), ("v_out", v_out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 \
+                or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    dim = c.dim()
+    n = int(c.shape[0])
+    if u_in.dim() != dim + 1 or tuple(u_in.shape[1:]) != tuple(c.shape):
+        raise ValueError("u_in must be [N, *c.shape]")
+    for t in (v_in, u_out, v_out):
+        if t.shape != u_in.shape:
+            raise ValueError("u_in, v_in, u_out, v_out must have the same shape")
+    msg = ctypes.create_string_buffer(512)
+    st = load().pr_fine_all_slices_noalloc(
+        dim, n, int(u_in.shape[0]), ctypes.c_void_p(c.data_ptr()), dt_f, m_f,
+        ctypes.c_void_p(u_in.data_ptr()), ctypes.c_void_p(v_in.data_ptr()),
+        ctypes.c_void_p(u_out.data_ptr()), ctypes.c_void_p(v_out.data_ptr()),
+        ctypes.c_void_p(_stream_ptr(stream)), msg, len(msg))
+    if st != 0:
+        raise PrError(st, msg.value.decode())
