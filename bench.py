@@ -188,17 +188,25 @@ def dist_env():
     return rank, world, local
 
 
-def workload_for(cfg: str) -> W.Workload:
+def workload_for(cfg: str, slices: int = 0) -> W.Workload:
+    """The configuration's workload; slices > 0 keeps the grid, medium and
+    time step but propagates only that many slices (small profiling runs)."""
     if cfg not in ("2", "3"):
         raise SystemExit("--config must be 2 or 3 (2D FP32 sweeps)")
-    return W.CONFIGS[cfg]()
+    w = W.CONFIGS[cfg]()
+    if slices and slices != w.n_slices:
+        m_f = w.m_f
+        w.t_final = w.t_final * slices / w.n_slices
+        w.n_slices = slices
+        w.m_f_fixed = m_f
+        w.name = f"{w.name}[{slices} slices]"
+    return w
 
 
 def workload_desc(w: W.Workload) -> dict:
     return {"workload": w.name, "dim": w.dim, "n_fine": w.n_fine, "slices": w.n_slices,
             "m_f": w.m_f, "point_updates_per_step": w.point_steps_per_sweep(),
-            "inputs": "seeded Gaussian-pulse slice states, c field of the configuration",
-            "l2": "inputs larger than L2 (no flush)"}
+            "inputs": "seeded Gaussian-pulse slice states, c field of the configuration"}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -206,7 +214,7 @@ def run_reference(a) -> int:
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    w = workload_for(a.config)
+    w = workload_for(a.config, a.slices)
     procs = oracle_procs()
     steps_per_sample = max(4, min(w.m_f, 64))
     smp = OracleSampler(w, procs, steps_per_sample)
@@ -239,7 +247,7 @@ def run_reference(a) -> int:
 # ---------------------------------------------------------------- our arm
 def run_ours(a) -> int:
     rank, world, local = dist_env()
-    w = workload_for(a.config)
+    w = workload_for(a.config, a.slices)
     # the oracle pool is spawned before any CUDA call
     smp = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -277,27 +285,48 @@ def run_ours(a) -> int:
         binding.pr_fine_all_slices(ctx, u_in, v_in, u_out, v_out)
     binding.pr_check(ctx)
 
+    # between timed steps: inputs larger than L2, or an explicit L2 flush
+    l2_bytes = torch.cuda.get_device_properties(dev).L2_cache_size
+    in_bytes = 2 * u_in.numel() * 4
+    flush = a.l2_flush == "on" or (a.l2_flush == "auto" and in_bytes < 2 * l2_bytes)
+    flush_buf = torch.empty(max(2 * l2_bytes, 1 << 28) // 4, dtype=torch.float32, device=dev) if flush else None
+
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     binding.pr_profile(ctx, True)
-    ev0.record(stream)
-    for _ in range(a.steps):
-        binding.pr_fine_all_slices(ctx, u_in, v_in, u_out, v_out)
-    ev1.record(stream)
-    barrier()
+    if flush:
+        evs = []
+        for _ in range(a.steps):
+            flush_buf.fill_(1.0)
+            e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e_a.record(stream)
+            binding.pr_fine_all_slices(ctx, u_in, v_in, u_out, v_out)
+            e_b.record(stream)
+            evs.append((e_a, e_b))
+        barrier()
+        ms = sum(e_a.elapsed_time(e_b) for e_a, e_b in evs)
+    else:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(a.steps):
+            binding.pr_fine_all_slices(ctx, u_in, v_in, u_out, v_out)
+        ev1.record(stream)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
     binding.pr_profile(ctx, False)
     clk = clocks.stop()
     binding.pr_check(ctx)
-    ms = ev0.elapsed_time(ev1)
     fused_n, fused_ms = binding.pr_profile_read(ctx, 0)
     single_n, single_ms = binding.pr_profile_read(ctx, 1)
     if pg is not None:
         t = torch.tensor([ms], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
+    l2_note = (f"L2 flushed between timed steps ({flush_buf.numel() * 4 >> 20} MiB write), "
+               f"steps timed one by one" if flush else
+               f"inputs larger than L2 ({in_bytes >> 20} MiB vs {l2_bytes >> 20} MiB), no flush")
     units = w.point_steps_per_sweep()
     value = world * units * a.steps / (ms * 1e-3)
 
@@ -357,7 +386,7 @@ def run_ours(a) -> int:
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": dict(workload_desc(w), block_depth=info["block_depth"],
+            "config": dict(workload_desc(w), l2=l2_note, block_depth=info["block_depth"],
                            parallelism=f"replica per GPU x{world}"),
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -380,7 +409,11 @@ def main(argv=None) -> int:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="3")
     ap.add_argument("--block-depth", type=int, default=0, help="0 = library default")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="propagate only this many slices (smaller profiling runs; 0 = all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--l2-flush", choices=["auto", "on", "off"], default="auto",
+                    help="auto: flush L2 between timed steps when the inputs are smaller than 2x L2")
     a = ap.parse_args(argv)
     if a.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

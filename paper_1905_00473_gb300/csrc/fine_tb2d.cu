@@ -119,238 +119,320 @@ struct Smem {
     static constexpr size_t sh_row = (size_t)W * 4 * 2 + W;    // u_hi, u_t, residual
     static constexpr size_t deep_bytes = kRD * deep_row;
     static constexpr size_t sh_bytes = kRS * sh_row;
-    static constexpr size_t xbuf_bytes = (size_t)2 * (B + 1) * 2 * NT * 4;
+    static constexpr size_t xbuf_bytes = (size_t)3 * B * 2 * NT * 4;  // [3][B][2][NT]
     static constexpr size_t bar_bytes = (size_t)kRD * 8;
     static constexpr size_t total = deep_bytes + sh_bytes + xbuf_bytes + bar_bytes;
 };
 
+// Per-segment constants of one CTA's current row range.
+struct Seg {
+    const float* u_s;
+    const float* v_s;
+    const int8_t* r_s;
+    int64_t slice_off;   // slice * n^2
+    uint32_t base;       // ring index of local row 0
+    int ylo;             // global row of local row 0
+    int H, L, nload;
+};
+
+template <int NT, int B>
+struct Shared {
+    unsigned char* deep;   // [kRD][kappa W | D0 W]
+    unsigned char* shal;   // [kRS][u W | v W | r W]
+    float* xbuf;           // [3][B][2][NT]: edge columns of each level's output row
+    uint64_t* bars;        // [kRD]
+};
+
+// One row iteration of the pipeline; PH = i mod 3 selects the register ring
+// slots and the xbuf buffer at compile time.  Register rings per level l:
+//   R[l][.]  du rows of level l's input: centre = slot PH, south = (PH+2)%3,
+//            north = (PH+1)%3 (written this iteration by the level below)
+//   VV[l][.] u_t of level l's input row: read (PH+2)%3, written PH
+// Returns true when some thread's bounded wait gave up.
+template <int NT, int B, bool MID, int PH>
+__device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, const Shared<NT, B>& sh,
+                                          int i, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
+                                          int& timed_out, uint32_t& consumed, uint64_t pol_first,
+                                          uint64_t pol_last, uint64_t pol_norm) {
+    using S = Smem<NT, B>;
+    constexpr int W = S::W;
+    constexpr int CUR = PH, PRV = (PH + 2) % 3, NXT = (PH + 1) % 3;
+    const int t = threadIdx.x;
+    const int n = p.n;
+    const int L = MID ? B : sg.L;
+    const uint32_t q = sg.base + (uint32_t)i;
+    auto gy = [&](int rho) { int y = sg.ylo + rho; return y >= n ? y - n : y; };
+
+    // ---- producer: row i + kPrefetch into the rings ---------------------
+    if (t == 0 && i + kPrefetch < sg.nload) {
+        const int rho = i + kPrefetch;
+        const uint32_t qq = sg.base + (uint32_t)rho;
+        const int64_t off = (int64_t)gy(rho) * n;
+        uint64_t* bar = &sh.bars[qq & (kRD - 1)];
+        unsigned char* drow = sh.deep + (size_t)(qq & (kRD - 1)) * S::deep_row;
+        unsigned char* srow = sh.shal + (size_t)(qq % kRS) * S::sh_row;
+        const uint32_t row_bytes = (uint32_t)W * 4;
+        mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)W : 0u));
+        bulk_g2s(drow, p.kap + off, row_bytes, bar, pol_last);
+        bulk_g2s(srow, sg.u_s + off, row_bytes, bar, pol_norm);
+        bulk_g2s(srow + W * 4, sg.v_s + off, row_bytes, bar, pol_first);
+        if (sg.r_s) bulk_g2s(srow + W * 8, sg.r_s + off, (uint32_t)W, bar, pol_first);
+    }
+
+    // ---- the finished row's u_hi, fetched early from L2 ------------------
+    const int rho_out = i - B;
+    const bool do_out = rho_out >= L && rho_out < L + sg.H;
+    int64_t off_out = 0;
+    float4 u0o = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (do_out) {
+        off_out = sg.slice_off + (int64_t)gy(rho_out) * n + kCpt * t;
+        u0o = __ldcs((const float4*)(p.u_in + off_out));
+    }
+
+    // ---- load stage: row i arrives; D0 of row i-1 -------------------------
+    float d0n[kCpt] = {0.f, 0.f, 0.f, 0.f};
+    const bool have_row = i < sg.nload;
+    if (have_row) {
+        if (!timed_out && !mbar_wait_bounded(&sh.bars[q & (kRD - 1)], (q / kRD) & 1u, 2000000000ull)) {
+            atomicExch(p.flag, 1);
+            timed_out = 1;
+        }
+        consumed = q + 1;
+        const unsigned char* s0 = sh.shal + (size_t)(q % kRS) * S::sh_row;
+        const float4 u4 = *(const float4*)(s0 + 16 * t);
+        const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
+        if (sg.r_s) {
+            const char4 r4 = *(const char4*)(s0 + W * 8 + kCpt * t);
+            const int8_t rr[4] = {(int8_t)r4.x, (int8_t)r4.y, (int8_t)r4.z, (int8_t)r4.w};
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) R[0][NXT][k] = pr_resid_decode(rr[k], uu[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) R[0][NXT][k] = 0.0f;
+        }
+        if (i >= 1) {
+            const float* s1 = (const float*)(sh.shal + (size_t)((q - 1) % kRS) * S::sh_row);
+            const float* s2 = (const float*)(sh.shal + (size_t)((i >= 2 ? q - 2 : q - 1) % kRS) * S::sh_row);
+            const float4 a = *(const float4*)(s1 + kCpt * t);
+            const float4 b2 = *(const float4*)(s2 + kCpt * t);
+            const float c[4] = {a.x, a.y, a.z, a.w};
+            const float s2v[4] = {b2.x, b2.y, b2.z, b2.w};
+            const float xl = s1[(kCpt * t + W - 1) % W], xrr = s1[(kCpt * t + kCpt) % W];
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) {
+                const float left = k == 0 ? xl : c[k - 1];
+                const float right = k == kCpt - 1 ? xrr : c[k + 1];
+                d0n[k] = ((left - c[k]) + (right - c[k])) + ((s2v[k] - c[k]) + (uu[k] - c[k]));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kCpt; ++k) R[0][NXT][k] = 0.0f;
+    }
+
+    // ---- levels: level l advances row i-1-l ------------------------------
+    const float* xr = sh.xbuf + (size_t)PRV * B * 2 * NT;
+    const int tl = (t + NT - 1) % NT, tr = (t + 1) % NT;
+    const float dt = p.dt;
+    float dout[kCpt], vout[kCpt];
+#pragma unroll
+    for (int l = 0; l < B; ++l) {
+        const uint32_t qr = q - 1u - (uint32_t)l;
+        const float* drow = (const float*)(sh.deep + (size_t)(qr & (kRD - 1)) * S::deep_row);
+        float vin[kCpt];
+        if (l == 0) {
+            const float4 v4 = *(const float4*)(sh.shal + (size_t)(qr % kRS) * S::sh_row + W * 4 + 16 * t);
+            vin[0] = v4.x; vin[1] = v4.y; vin[2] = v4.z; vin[3] = v4.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) vin[k] = VV[l][PRV][k];
+        }
+        float dn[kCpt], vn[kCpt];
+        if (MID || l < L) {
+            const float4 k4 = *(const float4*)(drow + kCpt * t);
+            float kk[4] = {k4.x, k4.y, k4.z, k4.w};
+            float dd[4];
+            if (l == 0) {
+#pragma unroll
+                for (int k = 0; k < kCpt; ++k) dd[k] = d0n[k];
+            } else {
+                const float4 d4 = *(const float4*)(drow + W + kCpt * t);
+                dd[0] = d4.x; dd[1] = d4.y; dd[2] = d4.z; dd[3] = d4.w;
+            }
+            const float xl = xr[l * 2 * NT + NT + tl];
+            const float xrt = xr[l * 2 * NT + tr];
+            bool dr = true;
+            if (!MID) {
+                const int g = p.g0 + l;
+                if (g == 0 || g == p.m) {
+#pragma unroll
+                    for (int k = 0; k < kCpt; ++k) kk[k] *= 0.5f;
+                }
+                dr = g < p.m;
+            }
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) {
+                const float left = k == 0 ? xl : R[l][CUR][k - 1];
+                const float right = k == kCpt - 1 ? xrt : R[l][CUR][k + 1];
+                // D(u) = D0 + (du_S + du_N + du_W + du_E - 4 du_C); the fresh
+                // north row enters last to keep the level-to-level chain short
+                const float part = dd[k] + fmaf(-4.0f, R[l][CUR][k], (left + right) + R[l][PRV][k]);
+                vn[k] = fmaf(kk[k], part + R[l][NXT][k], vin[k]);
+                dn[k] = dr ? fmaf(dt, vn[k], R[l][CUR][k]) : R[l][CUR][k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) {
+                vn[k] = vin[k];
+                dn[k] = R[l][CUR][k];
+            }
+        }
+        if (l + 1 < B) {
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) {
+                R[l + 1][NXT][k] = dn[k];
+                VV[l + 1][CUR][k] = vn[k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) {
+                dout[k] = dn[k];
+                vout[k] = vn[k];
+            }
+        }
+    }
+
+    // ---- row i-B leaves the pipeline -------------------------------------
+    if (do_out) {
+        const float u0[4] = {u0o.x, u0o.y, u0o.z, u0o.w};
+        float uo[4];
+        if (MID || p.r_out) {
+            int8_t qq[4];
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) uo[k] = pr_sum_encode(u0[k], dout[k], &qq[k]);
+            *(char4*)(p.r_out + off_out) = make_char4(qq[0], qq[1], qq[2], qq[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) uo[k] = u0[k] + dout[k];
+        }
+        *(float4*)(p.u_out + off_out) = make_float4(uo[0], uo[1], uo[2], uo[3]);
+        *(float4*)(p.v_out + off_out) = make_float4(vout[0], vout[1], vout[2], vout[3]);
+    }
+
+    // ---- shared stores, read only in later iterations ----------------------
+    float* xw = sh.xbuf + (size_t)CUR * B * 2 * NT;
+#pragma unroll
+    for (int l = 0; l < B; ++l) {
+        if (MID || l < L) {   // level l's input rows: edges read by level l next iteration
+            xw[l * 2 * NT + t] = R[l][NXT][0];
+            xw[l * 2 * NT + NT + t] = R[l][NXT][kCpt - 1];
+        }
+    }
+    if (have_row && i >= 1) {
+        float* dd = (float*)(sh.deep + (size_t)((q - 1) & (kRD - 1)) * S::deep_row) + W;
+        *(float4*)(dd + kCpt * t) = make_float4(d0n[0], d0n[1], d0n[2], d0n[3]);
+    }
+    // one barrier per row; it also makes the abort decision uniform
+    return __syncthreads_or(timed_out) != 0;
+}
+
 template <int NT, int B, bool MID>
 __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     using S = Smem<NT, B>;
-    constexpr int W = S::W;
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* deep = smem;                                            // [kRD][kappa W | D0 W]
-    unsigned char* shal = smem + S::deep_bytes;                            // [kRS][u W | v W | r W]
-    float* xbuf = (float*)(smem + S::deep_bytes + S::sh_bytes);            // [2][B+1][2][NT]
-    uint64_t* bars = (uint64_t*)(smem + S::deep_bytes + S::sh_bytes + S::xbuf_bytes);
+    Shared<NT, B> sh;
+    sh.deep = smem;
+    sh.shal = smem + S::deep_bytes;
+    sh.xbuf = (float*)(smem + S::deep_bytes + S::sh_bytes);
+    sh.bars = (uint64_t*)(smem + S::deep_bytes + S::sh_bytes + S::xbuf_bytes);
 
     const int t = threadIdx.x;
     const int n = p.n;
     const int64_t pts = (int64_t)n * n;
     const int L = MID ? B : p.levels;
-    const float dt = p.dt;
-    const int tl = (t + NT - 1) % NT, tr = (t + 1) % NT;
-    const int cl = (kCpt * t + W - 1) % W, cr = (kCpt * t + kCpt) % W;
 
     if (t == 0) {
-        for (int s = 0; s < kRD; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < kRD; ++s) mbar_init(&sh.bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-
     uint64_t pol_first = 0, pol_last = 0, pol_norm = 0;
     if (t == 0) {
         pol_first = policy(0);
         pol_last = policy(1);
         pol_norm = policy(2);
     }
-    const uint32_t row_bytes = (uint32_t)W * 4;
-    const uint32_t tx_bytes = 3 * row_bytes + (p.r_in ? (uint32_t)W : 0u);
 
     const int64_t r_begin = p.rows_total * blockIdx.x / gridDim.x;
     const int64_t r_end = p.rows_total * (blockIdx.x + 1) / gridDim.x;
-
-    uint32_t issued = 0, consumed = 0, it_par = 0;
+    uint32_t issued = 0, consumed = 0;
     int timed_out = 0;
     bool aborted = false;
 
     for (int64_t seg0 = r_begin; seg0 < r_end && !aborted;) {
+        Seg sg;
         const int64_t slice = seg0 / n;
         const int ya = (int)(seg0 - slice * n);
         const int64_t seg1 = min(r_end, (slice + 1) * (int64_t)n);
-        const int H = (int)(seg1 - seg0);
+        sg.H = (int)(seg1 - seg0);
         seg0 = seg1;
-        const int nload = H + 2 * L;
-        const int niter = H + L + B;
-        const float* u_s = p.u_in + slice * pts;
-        const float* v_s = p.v_in + slice * pts;
-        const int8_t* r_s = p.r_in ? p.r_in + slice * pts : nullptr;
-        const uint32_t base = issued;
-        int ylo = ya - L;                    // global row of local row 0 (mod n)
-        ylo %= n;
-        if (ylo < 0) ylo += n;
-        auto gy = [&](int rho) { int y = ylo + rho; return y >= n ? y - n : y; };
+        sg.L = L;
+        sg.nload = sg.H + 2 * L;
+        sg.slice_off = slice * pts;
+        sg.u_s = p.u_in + slice * pts;
+        sg.v_s = p.v_in + slice * pts;
+        sg.r_s = p.r_in ? p.r_in + slice * pts : nullptr;
+        sg.base = issued;
+        int ylo = (ya - L) % n;
+        sg.ylo = ylo < 0 ? ylo + n : ylo;
+        const int niter = sg.H + L + B;
 
-        auto issue = [&](int rho) {
-            const uint32_t q = base + (uint32_t)rho;
-            const int64_t off = (int64_t)gy(rho) * n;
-            uint64_t* bar = &bars[q & (kRD - 1)];
-            unsigned char* drow = deep + (size_t)(q & (kRD - 1)) * S::deep_row;
-            unsigned char* srow = shal + (size_t)(q % kRS) * S::sh_row;
-            mbar_expect_tx(bar, tx_bytes);
-            bulk_g2s(drow, p.kap + off, row_bytes, bar, pol_last);
-            bulk_g2s(srow, u_s + off, row_bytes, bar, pol_norm);
-            bulk_g2s(srow + W * 4, v_s + off, row_bytes, bar, pol_first);
-            if (r_s) bulk_g2s(srow + W * 8, r_s + off, (uint32_t)W, bar, pol_first);
-        };
-        if (t == 0)
-            for (int rho = 0; rho < kPrefetch && rho < nload; ++rho) issue(rho);
-        issued += (uint32_t)nload;
+        if (t == 0) {
+            for (int rho = 0; rho < kPrefetch && rho < sg.nload; ++rho) {
+                const uint32_t qq = sg.base + (uint32_t)rho;
+                int y = sg.ylo + rho;
+                if (y >= n) y -= n;
+                const int64_t off = (int64_t)y * n;
+                uint64_t* bar = &sh.bars[qq & (kRD - 1)];
+                unsigned char* drow = sh.deep + (size_t)(qq & (kRD - 1)) * S::deep_row;
+                unsigned char* srow = sh.shal + (size_t)(qq % kRS) * S::sh_row;
+                const uint32_t row_bytes = (uint32_t)S::W * 4;
+                mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)S::W : 0u));
+                bulk_g2s(drow, p.kap + off, row_bytes, bar, pol_last);
+                bulk_g2s(srow, sg.u_s + off, row_bytes, bar, pol_norm);
+                bulk_g2s(srow + S::W * 4, sg.v_s + off, row_bytes, bar, pol_first);
+                if (sg.r_s) bulk_g2s(srow + S::W * 8, sg.r_s + off, (uint32_t)S::W, bar, pol_first);
+            }
+        }
+        issued += (uint32_t)sg.nload;
 
-        float P1[B][kCpt], P2[B][kCpt], V[B + 1][kCpt];
+        float R[B][3][kCpt], VV[B][3][kCpt];
 #pragma unroll
         for (int l = 0; l < B; ++l)
 #pragma unroll
-            for (int k = 0; k < kCpt; ++k) P1[l][k] = P2[l][k] = 0.0f;
+            for (int s = 0; s < 3; ++s)
 #pragma unroll
-        for (int l = 0; l <= B; ++l)
-#pragma unroll
-            for (int k = 0; k < kCpt; ++k) V[l][k] = 0.0f;
+                for (int k = 0; k < kCpt; ++k) R[l][s][k] = VV[l][s][k] = 0.0f;
 
-        for (int i = 0; i < niter; ++i) {
-            if (t == 0 && i + kPrefetch < nload) issue(i + kPrefetch);
-            const uint32_t par = it_par & 1u;
-            float* xw = xbuf + (size_t)par * (B + 1) * 2 * NT;
-            const float* xr = xbuf + (size_t)(par ^ 1u) * (B + 1) * 2 * NT;
-            const uint32_t q = base + (uint32_t)i;   // ring index of row i
-
-            float fresh[B + 1][kCpt];
-            // ---- load stage: row i arrives, D0 of row i-1 -----------------
-            if (i < nload) {
-                if (!timed_out && !mbar_wait_bounded(&bars[q & (kRD - 1)], (q / kRD) & 1u, 2000000000ull)) {
-                    atomicExch(p.flag, 1);
-                    timed_out = 1;
-                }
-                consumed = q + 1;
-                const unsigned char* s0 = shal + (size_t)(q % kRS) * S::sh_row;
-                const float4 u4 = *(const float4*)(s0 + 16 * t);
-                const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
-                if (r_s) {
-                    const char4 r4 = *(const char4*)(s0 + W * 8 + kCpt * t);
-                    const int8_t rr[4] = {(int8_t)r4.x, (int8_t)r4.y, (int8_t)r4.z, (int8_t)r4.w};
-#pragma unroll
-                    for (int k = 0; k < kCpt; ++k) fresh[0][k] = pr_resid_decode(rr[k], uu[k]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < kCpt; ++k) fresh[0][k] = 0.0f;
-                }
-                xw[t] = fresh[0][0];
-                xw[NT + t] = fresh[0][kCpt - 1];
-                if (i >= 1) {
-                    const float* s1 = (const float*)(shal + (size_t)((q - 1) % kRS) * S::sh_row);
-                    const float* s2 = (const float*)(shal + (size_t)((i >= 2 ? q - 2 : q - 1) % kRS) * S::sh_row);
-                    const float4 a = *(const float4*)(s1 + kCpt * t);
-                    const float4 b2 = *(const float4*)(s2 + kCpt * t);
-                    const float c[4] = {a.x, a.y, a.z, a.w};
-                    const float s2v[4] = {b2.x, b2.y, b2.z, b2.w};
-                    const float xl = s1[cl], xrr = s1[cr];
-                    float d0[4];
-#pragma unroll
-                    for (int k = 0; k < kCpt; ++k) {
-                        const float left = k == 0 ? xl : c[k - 1];
-                        const float right = k == kCpt - 1 ? xrr : c[k + 1];
-                        d0[k] = ((left - c[k]) + (right - c[k])) + ((s2v[k] - c[k]) + (uu[k] - c[k]));
-                    }
-                    float* dd = (float*)(deep + (size_t)((q - 1) & (kRD - 1)) * S::deep_row) + W;
-                    *(float4*)(dd + kCpt * t) = make_float4(d0[0], d0[1], d0[2], d0[3]);
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kCpt; ++k) fresh[0][k] = 0.0f;
+        int i = 0;
+        for (; i + 3 <= niter; i += 3) {
+            if (tb2d_iter<NT, B, MID, 0>(p, sg, sh, i, R, VV, timed_out, consumed, pol_first, pol_last, pol_norm) ||
+                tb2d_iter<NT, B, MID, 1>(p, sg, sh, i + 1, R, VV, timed_out, consumed, pol_first, pol_last, pol_norm) ||
+                tb2d_iter<NT, B, MID, 2>(p, sg, sh, i + 2, R, VV, timed_out, consumed, pol_first, pol_last, pol_norm)) {
+                aborted = true;
+                break;
             }
-
-            // ---- levels ---------------------------------------------------
-            float VN[B + 1][kCpt];
-#pragma unroll
-            for (int l = 0; l < B; ++l) {
-                const uint32_t qr = q - 1u - (uint32_t)l;   // ring index of this level's row
-                const float* drow = (const float*)(deep + (size_t)(qr & (kRD - 1)) * S::deep_row);
-                float vin[kCpt];
-                if (l == 0) {
-                    const float4 v4 = *(const float4*)(shal + (size_t)(qr % kRS) * S::sh_row + W * 4 + 16 * t);
-                    vin[0] = v4.x; vin[1] = v4.y; vin[2] = v4.z; vin[3] = v4.w;
-                } else {
-#pragma unroll
-                    for (int k = 0; k < kCpt; ++k) vin[k] = V[l][k];
-                }
-                if (MID || l < L) {
-                    const float4 k4 = *(const float4*)(drow + kCpt * t);
-                    const float4 d4 = *(const float4*)(drow + W + kCpt * t);
-                    float kk[4] = {k4.x, k4.y, k4.z, k4.w};
-                    const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
-                    const float xl = xr[l * 2 * NT + NT + tl];
-                    const float xrt = xr[l * 2 * NT + tr];
-                    bool dr = true;
-                    if (!MID) {
-                        const int g = p.g0 + l;
-                        if (g == 0 || g == p.m) {
-#pragma unroll
-                            for (int k = 0; k < kCpt; ++k) kk[k] *= 0.5f;
-                        }
-                        dr = g < p.m;
-                    }
-#pragma unroll
-                    for (int k = 0; k < kCpt; ++k) {
-                        const float left = k == 0 ? xl : P1[l][k - 1];
-                        const float right = k == kCpt - 1 ? xrt : P1[l][k + 1];
-                        // D(u) = D0 + (du_S + du_N + du_W + du_E - 4 du_C); the fresh
-                        // north row enters last to keep the level-to-level chain short
-                        const float part = dd[k] + fmaf(-4.0f, P1[l][k], (left + right) + P2[l][k]);
-                        const float vn = fmaf(kk[k], part + fresh[l][k], vin[k]);
-                        VN[l + 1][k] = vn;
-                        fresh[l + 1][k] = dr ? fmaf(dt, vn, P1[l][k]) : P1[l][k];
-                    }
-                    if (l + 1 < L) {
-                        xw[(l + 1) * 2 * NT + t] = fresh[l + 1][0];
-                        xw[(l + 1) * 2 * NT + NT + t] = fresh[l + 1][kCpt - 1];
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < kCpt; ++k) {
-                        VN[l + 1][k] = vin[k];
-                        fresh[l + 1][k] = P1[l][k];
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < kCpt; ++k) {
-                    P2[l][k] = P1[l][k];
-                    P1[l][k] = fresh[l][k];
-                }
-            }
-
-            // ---- row i-B leaves the pipeline ------------------------------
-            const int rho_out = i - B;
-            if (rho_out >= L && rho_out < L + H) {
-                const int64_t off = slice * pts + (int64_t)gy(rho_out) * n + kCpt * t;
-                const float4 u4 = __ldcs((const float4*)(p.u_in + off));
-                const float u0[4] = {u4.x, u4.y, u4.z, u4.w};
-                float uo[4];
-                if (MID || p.r_out) {
-                    int8_t qq[4];
-#pragma unroll
-                    for (int k = 0; k < kCpt; ++k) uo[k] = pr_sum_encode(u0[k], fresh[B][k], &qq[k]);
-                    *(char4*)(p.r_out + off) = make_char4(qq[0], qq[1], qq[2], qq[3]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < kCpt; ++k) uo[k] = u0[k] + fresh[B][k];
-                }
-                *(float4*)(p.u_out + off) = make_float4(uo[0], uo[1], uo[2], uo[3]);
-                *(float4*)(p.v_out + off) = make_float4(VN[B][0], VN[B][1], VN[B][2], VN[B][3]);
-            }
-#pragma unroll
-            for (int l = 1; l <= B; ++l)
-#pragma unroll
-                for (int k = 0; k < kCpt; ++k) V[l][k] = VN[l][k];
-            ++it_par;
-            // one barrier per row; it also makes the abort decision uniform
-            if (__syncthreads_or(timed_out)) { aborted = true; break; }
         }
+        if (!aborted && i < niter)
+            aborted = tb2d_iter<NT, B, MID, 0>(p, sg, sh, i, R, VV, timed_out, consumed, pol_first, pol_last, pol_norm);
+        if (!aborted && i + 1 < niter)
+            aborted = tb2d_iter<NT, B, MID, 1>(p, sg, sh, i + 1, R, VV, timed_out, consumed, pol_first, pol_last, pol_norm);
     }
     if (aborted && t == 0) {
         // let copies still in flight land before the CTA's shared memory is released
         for (uint32_t q = consumed; q < issued; ++q)
-            (void)mbar_wait_bounded(&bars[q & (kRD - 1)], (q / kRD) & 1u, 100000000ull);
+            (void)mbar_wait_bounded(&sh.bars[q & (kRD - 1)], (q / kRD) & 1u, 100000000ull);
     }
 }
 
