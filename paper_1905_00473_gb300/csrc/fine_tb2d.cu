@@ -97,6 +97,38 @@ __device__ __forceinline__ uint64_t policy(int kind) {
     return p;
 }
 
+// Packed FP32 pairs (Blackwell f32x2 arithmetic): two lanes of one 64-bit
+// register, each lane rounded exactly like the scalar instruction.
+#ifndef PR_TB2D_PACKED
+#define PR_TB2D_PACKED 1
+#endif
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float a, float b) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(f2_t x) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+    return a;
+}
+__device__ __forceinline__ float f2_hi(f2_t x) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+    return b;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 struct Tb2dParams {
     const float* u_in;
     const float* v_in;
@@ -270,6 +302,31 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
                 }
                 dr = g < p.m;
             }
+#if PR_TB2D_PACKED
+            {
+                // columns (0,1) and (2,3) as f32x2 pairs; the horizontal
+                // neighbour sums cross the pairs and stay scalar
+                const float* C = R[l][CUR];
+                const float h0 = xl + C[1], h1 = C[0] + C[2], h2 = C[1] + C[3], h3 = C[2] + xrt;
+                const f2_t m4 = f2_pack(-4.0f, -4.0f), dt2 = f2_pack(dt, dt);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 2 * h;
+                    const f2_t cc = f2_pack(C[k], C[k + 1]);
+                    const f2_t hs = f2_add(h == 0 ? f2_pack(h0, h1) : f2_pack(h2, h3),
+                                           f2_pack(R[l][PRV][k], R[l][PRV][k + 1]));
+                    const f2_t part = f2_add(f2_pack(dd[k], dd[k + 1]), f2_fma(m4, cc, hs));
+                    const f2_t v2 = f2_fma(f2_pack(kk[k], kk[k + 1]),
+                                           f2_add(part, f2_pack(R[l][NXT][k], R[l][NXT][k + 1])),
+                                           f2_pack(vin[k], vin[k + 1]));
+                    const f2_t d2 = dr ? f2_fma(dt2, v2, cc) : cc;
+                    vn[k] = f2_lo(v2);
+                    vn[k + 1] = f2_hi(v2);
+                    dn[k] = f2_lo(d2);
+                    dn[k + 1] = f2_hi(d2);
+                }
+            }
+#else
 #pragma unroll
             for (int k = 0; k < kCpt; ++k) {
                 const float left = k == 0 ? xl : R[l][CUR][k - 1];
@@ -280,6 +337,7 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
                 vn[k] = fmaf(kk[k], part + R[l][NXT][k], vin[k]);
                 dn[k] = dr ? fmaf(dt, vn[k], R[l][CUR][k]) : R[l][CUR][k];
             }
+#endif
         } else {
 #pragma unroll
             for (int k = 0; k < kCpt; ++k) {

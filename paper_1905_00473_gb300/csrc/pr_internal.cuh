@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/pr.h"
+#include "pr.h"
 
 struct pr_ctx {
     int device = 0;
