@@ -135,7 +135,8 @@ def test_reconstruction_errors_match_the_papers_table():
 
 def test_planted_mistakes_are_caught(monkeypatch):
     """A sign error in grad2func, a restriction shifted by one node, and a
-    Nyquist mode that is not split each fail one of the pins above."""
+    Nyquist coefficient copied to both sides without halving each fail one of
+    the pins above."""
     import oracle.transfer as T
     n = 32
     x = np.arange(n) / n
@@ -150,6 +151,6 @@ def test_planted_mistakes_are_caught(monkeypatch):
     Uc = np.cos(math.pi * 8 * np.arange(8) / 8)
     Uh = np.fft.fft(Uc)
     Y = np.zeros(32, dtype=complex)
-    Y[4] = Uh[4]                          # Nyquist kept on one side only
+    Y[4] = Y[28] = Uh[4]                  # Nyquist on both sides, not halved
     unsplit = np.real(np.fft.ifft(Y)) * 4
     assert np.max(np.abs(unsplit - T.interpolate(Uc, 4))) > 0.1
