@@ -119,6 +119,58 @@ const char* pr_last_error(const pr_ctx* ctx);
 pr_status pr_fine_all_slices(pr_ctx* ctx, const void* u_in, const void* v_in, void* u_out,
                              void* v_out, int n_begin, int n_end, void* stream);
 
+/* Phase correctors of pr_iterate (Alg. 3 and its variants, Sec. 6.2):
+ * PR_CORR_PROCRUSTES  theta = I Lambda^dagger Omega Lambda with Omega = X Y^T from Alg. 1;
+ * PR_CORR_OMEGA1      Omega = 1, theta = I Lambda^dagger Lambda (Sec. 6.2);
+ * PR_CORR_PLAIN       theta = I, plain parareal on the two grids (Sec. 1). */
+enum { PR_CORR_PROCRUSTES = 0, PR_CORR_OMEGA1 = 1, PR_CORR_PLAIN = 2 };
+
+/* pr_coarse_sweep -- the coarse half of Alg. 3's parallel phase,
+ * [U_n, U_t n] = C [R u_{n-1}, R u_t n-1], for slices [n_begin, n_end).
+ *  u, v          fine states [N][n^d] (dtype), read.
+ *  U_out, V_out  coarse states [N][(n/ratio)^d] (dtype), written for the range.
+ * R is injection onto the coarse nodes (Sec. 6); C is m_C velocity-Verlet
+ * steps of dt_c on the coarse grid with c taken at the coarse nodes (Sec. 3.1),
+ * run by the same kernels as F. */
+pr_status pr_coarse_sweep(pr_ctx* ctx, const void* u, const void* v, void* U_out, void* V_out,
+                          int n_begin, int n_end, void* stream);
+
+/* pr_iterate -- the proposed method, Alg. 3, for K iterations.
+ *  u0, p0      initial state [n^d] (dtype, device).
+ *  K           iterations (K = 0 returns the initial guess I C R u_{n-1}).
+ *  corrector   PR_CORR_*.
+ *  u_slices, v_slices  [N+1][n^d] (dtype, device): on return the states
+ *              u^{K+1}_n, n = 0..N (u^{K+1}_0 = [u0, p0]).
+ *  resid_hist  HOST double[K] or NULL: ||F - Omega G||_F / ||F||_F of each
+ *              iteration's data after the update (0 without Procrustes).
+ *  rank_hist   HOST int[K] or NULL: retained singular values s.
+ * Fine sweeps run in the context dtype; Lambda, Omega, Lambda^dagger, I, the
+ * data matrices and the SVD in FP64 (cuFFT, cuBLAS, cuSOLVER for the FFTs and
+ * the dense factorisations).  The correction of a slice is applied to the
+ * difference Lambda w - Lambda U_n with zero mode sum w - sum U_n, which by
+ * linearity equals Alg. 3's two applications.  Synchronises the stream.
+ * Requires grad_order 2, 4, 6 or 8. */
+pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector,
+                     void* u_slices, void* v_slices, double* resid_hist, int* rank_hist,
+                     void* stream);
+
+/* pr_procrustes_correct -- UpdateSVD (Alg. 1): M <- M + F G^T with the
+ * context's truncated SVD M = X Sigma Y^T (rank cut sigma_i/sigma_max > tol).
+ *  Fcols, Gcols  DEVICE double [ncols][(d+1) n_c^d], one column per slice
+ *                (eq. matrixF / matrixG: [nabla_h w ; c^-1 w_t], x-derivative
+ *                block first), 1 <= ncols <= N.
+ * Synchronises the stream. */
+pr_status pr_procrustes_correct(pr_ctx* ctx, const double* Fcols, const double* Gcols, int ncols,
+                                void* stream);
+
+/* pr_procrustes_apply -- out = X Y^T g (the phase corrector Omega of Alg. 3)
+ * for a DEVICE double vector g of (d+1) n_c^d entries; *rank (host, may be
+ * NULL) receives s.  g == NULL only reports the rank. */
+pr_status pr_procrustes_apply(pr_ctx* ctx, const double* g, double* out, int* rank, void* stream);
+
+/* pr_procrustes_reset -- forget M (S empty, as at the start of Alg. 3). */
+pr_status pr_procrustes_reset(pr_ctx* ctx);
+
 /* pr_check -- synchronise `stream`, then report and clear a device-side error
  * flag set by a kernel whose bounded wait gave up (PR_ETIMEOUT), or a pending
  * CUDA error (PR_ECUDA). */

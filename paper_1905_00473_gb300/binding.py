@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(PKG, "_lib", "libpr.so")
 HEADER = os.path.join(ROOT, "include", "pr.h")
 
 PR_F32, PR_F64 = 0, 1
+PR_CORR_PROCRUSTES, PR_CORR_OMEGA1, PR_CORR_PLAIN = 0, 1, 2
 STATUS = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOMEM", 3: "PR_ECUDA", 4: "PR_ETIMEOUT",
           5: "PR_EUNSTABLE", 6: "PR_ENOTCONV"}
 
@@ -54,6 +55,12 @@ _SIGNATURES = {
     "pr_fine_all_slices_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _P,
                                                   ctypes.c_double, ctypes.c_int, _P, _P, _P, _P,
                                                   _P, ctypes.c_char_p, ctypes.c_size_t]),
+    "pr_coarse_sweep": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
+    "pr_iterate": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _P]),
+    "pr_procrustes_correct": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "pr_procrustes_apply": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
+    "pr_procrustes_reset": (ctypes.c_int, [_P]),
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double)]),
@@ -99,9 +106,9 @@ def _check(status: int, ctx_ptr) -> None:
 class Context:
     """Owns a pr_ctx; methods mirror the C entry points that take a context."""
 
-    def __init__(self, handle: int, dim: int, n: int, N: int, dtype: int):
+    def __init__(self, handle: int, dim: int, n: int, N: int, dtype: int, ratio: int = 1):
         self.handle = ctypes.c_void_p(handle)
-        self.dim, self.n, self.N, self.dtype = dim, n, N, dtype
+        self.dim, self.n, self.N, self.dtype, self.ratio = dim, n, N, dtype, ratio
 
     def __del__(self):
         try:
@@ -116,17 +123,28 @@ class Context:
         import torch
         return torch.float32 if self.dtype == PR_F32 else torch.float64
 
-    def _arr(self, t, name: str):
+    def _arr(self, t, name: str, count=None, dtype=None):
         import torch
         if not isinstance(t, torch.Tensor) or not t.is_cuda:
             raise TypeError(f"{name} must be a CUDA tensor")
-        if t.dtype != self.torch_dtype:
-            raise TypeError(f"{name} must be {self.torch_dtype}")
+        want = self.torch_dtype if dtype is None else dtype
+        if t.dtype != want:
+            raise TypeError(f"{name} must be {want}")
         if not t.is_contiguous():
             raise ValueError(f"{name} must be contiguous")
-        if t.numel() != self.N * self.n ** self.dim:
-            raise ValueError(f"{name} must hold N * n^dim = {self.N * self.n ** self.dim} values")
+        count = self.N * self.n ** self.dim if count is None else count
+        if t.numel() != count:
+            raise ValueError(f"{name} must hold {count} values")
         return ctypes.c_void_p(t.data_ptr())
+
+    @property
+    def n_coarse(self) -> int:
+        return self.n // self.ratio
+
+    @property
+    def rows(self) -> int:
+        """(d+1) n_c^d: length of an energy-component column."""
+        return (self.dim + 1) * self.n_coarse ** self.dim
 
 
 def pr_create(dim: int, n: int, ratio: int, c, dt_f: float, dt_c: float, N: int, T: float,
@@ -145,7 +163,7 @@ def pr_create(dim: int, n: int, ratio: int, c, dt_f: float, dt_c: float, N: int,
     st = lib.pr_create(ctypes.byref(g), ctypes.c_void_p(c.data_ptr()), dt_f, dt_c, N, T,
                        ctypes.byref(o), ctypes.byref(out))
     _check(st, None)
-    return Context(out.value, dim, n, N, dtype)
+    return Context(out.value, dim, n, N, dtype, ratio)
 
 
 def pr_fine_all_slices(ctx: Context, u_in, v_in, u_out, v_out, n_begin: int = 0,
@@ -215,3 +233,53 @@ def pr_fine_all_slices_noalloc(c, dt_f: float, m_f: int, u_in, v_in, u_out, v_ou
         ctypes.c_void_p(_stream_ptr(stream)), msg, len(msg))
     if st != 0:
         raise PrError(st, msg.value.decode())
+
+
+def pr_coarse_sweep(ctx: Context, u, v, U_out, V_out, n_begin: int = 0,
+                    n_end: Optional[int] = None, stream=None) -> None:
+    n_end = ctx.N if n_end is None else n_end
+    cc = ctx.N * ctx.n_coarse ** ctx.dim
+    st = load().pr_coarse_sweep(ctx.handle, ctx._arr(u, "u"), ctx._arr(v, "v"),
+                                ctx._arr(U_out, "U_out", cc), ctx._arr(V_out, "V_out", cc),
+                                n_begin, n_end, ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, ctx.handle)
+
+
+def pr_iterate(ctx: Context, u0, p0, K: int, corrector: int, u_slices, v_slices, stream=None):
+    """Runs Alg. 3; returns (residual history, rank history) as lists of length K."""
+    pts = ctx.n ** ctx.dim
+    res = (ctypes.c_double * max(1, K))()
+    rk = (ctypes.c_int * max(1, K))()
+    st = load().pr_iterate(ctx.handle, ctx._arr(u0, "u0", pts), ctx._arr(p0, "p0", pts), K,
+                           corrector, ctx._arr(u_slices, "u_slices", (ctx.N + 1) * pts),
+                           ctx._arr(v_slices, "v_slices", (ctx.N + 1) * pts), res, rk,
+                           ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, ctx.handle)
+    return list(res)[:K], list(rk)[:K]
+
+
+def pr_procrustes_correct(ctx: Context, Fcols, Gcols, stream=None) -> None:
+    """Fcols, Gcols: float64 CUDA tensors [ncols, rows] (one column per row of the tensor)."""
+    import torch
+    ncols = int(Fcols.shape[0])
+    st = load().pr_procrustes_correct(
+        ctx.handle, ctx._arr(Fcols, "Fcols", ncols * ctx.rows, torch.float64),
+        ctx._arr(Gcols, "Gcols", ncols * ctx.rows, torch.float64), ncols,
+        ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, ctx.handle)
+
+
+def pr_procrustes_apply(ctx: Context, g=None, out=None, stream=None) -> int:
+    """out = Omega g; returns the rank s."""
+    import torch
+    rk = ctypes.c_int()
+    gp = ctx._arr(g, "g", ctx.rows, torch.float64) if g is not None else None
+    op = ctx._arr(out, "out", ctx.rows, torch.float64) if out is not None else None
+    st = load().pr_procrustes_apply(ctx.handle, gp, op, ctypes.byref(rk),
+                                    ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, ctx.handle)
+    return rk.value
+
+
+def pr_procrustes_reset(ctx: Context) -> None:
+    _check(load().pr_procrustes_reset(ctx.handle), ctx.handle)

@@ -28,6 +28,13 @@ extern "C" const char* pr_last_error(const pr_ctx* ctx) {
 }
 
 static void free_all(pr_ctx* c) {
+    pr_driver_free(c);
+    if (c->coarse) {
+        free_all(c->coarse);
+        delete c->coarse;
+        c->coarse = nullptr;
+    }
+    cudaFree(c->c64);
     cudaFree(c->kappa);
     cudaFree(c->cinv2);
     for (int h = 0; h < 2; ++h) {
@@ -170,31 +177,71 @@ extern "C" pr_status pr_create(const pr_grid* grid, const void* c_dev, double dt
     if (cmax_coarse * dt_c * sd / (dx * grid->ratio) > 1.0)
         return pr_fail(nullptr, PR_EINVAL, "pr_create: coarse step violates CFL");
 
+    pr_ctx* ctx = nullptr;
+    pr_status st = pr_build_ctx(grid->dim, n, grid->ratio, N, T, dt_f, m_f, dt_c, m_c, o, c, &ctx);
+    if (st != PR_OK) return st;
+    if (grid->ratio >= 1) {
+        // the coarse propagator's own context: coarse grid, c at the coarse nodes,
+        // step dt_c, m_C steps per interval (Sec. 3.1)
+        const int64_t nc = n / grid->ratio;
+        int64_t cpts = 1;
+        for (int a = 0; a < grid->dim; ++a) cpts *= nc;
+        std::vector<double> cc(cpts);
+        for (int64_t J = 0; J < cpts; ++J) {
+            int64_t rem = J, idx = 0, stride = 1;
+            for (int a = 0; a < grid->dim; ++a) {
+                idx += (rem % nc) * grid->ratio * stride;
+                rem /= nc;
+                stride *= n;
+            }
+            cc[J] = c[idx];
+        }
+        pr_status sc = pr_build_ctx(grid->dim, nc, 1, N, T, dt_c, m_c, dt_c, m_c, o, cc, &ctx->coarse);
+        if (sc != PR_OK) {
+            pr_destroy(ctx);
+            return sc;
+        }
+    }
+    *out = ctx;
+    return PR_OK;
+}
+
+// Context of one grid: coefficient arrays and pass scratch for propagating
+// N slices with step dt (m steps per coupling interval).
+pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt, int m,
+                       double dt_c, int m_c, const pr_options& o, const std::vector<double>& c,
+                       pr_ctx** out) {
+    int64_t pts = 1;
+    for (int a = 0; a < dim; ++a) pts *= n;
+    const size_t esz = o.dtype == PR_F32 ? 4 : 8;
+    const double dx = 1.0 / (double)n;
+    double cmax = 0;
+    for (int64_t i = 0; i < pts; ++i) cmax = std::max(cmax, c[i]);
     pr_ctx* ctx = new pr_ctx();
     cudaGetDevice(&ctx->device);
-    ctx->dim = grid->dim;
+    ctx->dim = dim;
     ctx->n = n;
     ctx->pts = pts;
-    ctx->ratio = grid->ratio;
+    ctx->ratio = ratio;
     ctx->N = N;
     ctx->dtype = o.dtype;
     ctx->T = T;
-    ctx->dt_com = dt_com;
-    ctx->dt_f = dt_f;
+    ctx->dt_com = T / N;
+    ctx->dt_f = dt;
     ctx->dt_c = dt_c;
     ctx->dx = dx;
-    ctx->m_f = m_f;
+    ctx->m_f = m;
     ctx->m_c = m_c;
     ctx->cmax = cmax;
+    ctx->opts = o;
     int depth = o.block_depth;
     if (depth == 0) depth = 8;
     ctx->block_depth = pr_tb2d_supported(ctx, depth) ? depth : 1;
 
-    // coefficient arrays
     std::vector<char> kap(pts * esz);
     std::vector<double> cinv2(pts);
     for (int64_t i = 0; i < pts; ++i) {
-        const double k = c[i] * c[i] * dt_f / (dx * dx);
+        const double k = c[i] * c[i] * dt / (dx * dx);
         if (o.dtype == PR_F32) ((float*)kap.data())[i] = (float)k;
         else ((double*)kap.data())[i] = k;
         cinv2[i] = 1.0 / (c[i] * c[i]);
@@ -208,10 +255,13 @@ extern "C" pr_status pr_create(const pr_grid* grid, const void* c_dev, double dt
     cudaError_t e;
     if ((e = cudaMalloc(&ctx->kappa, pts * esz)) != cudaSuccess) return fail(e, "pr_create: alloc kappa");
     if ((e = cudaMalloc((void**)&ctx->cinv2, pts * 8)) != cudaSuccess) return fail(e, "pr_create: alloc cinv2");
+    if ((e = cudaMalloc((void**)&ctx->c64, pts * 8)) != cudaSuccess) return fail(e, "pr_create: alloc c");
     if ((e = cudaMemcpy(ctx->kappa, kap.data(), pts * esz, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "pr_create: upload kappa");
     if ((e = cudaMemcpy(ctx->cinv2, cinv2.data(), pts * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "pr_create: upload cinv2");
+    if ((e = cudaMemcpy(ctx->c64, c.data(), pts * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e, "pr_create: upload c");
     const size_t state = (size_t)N * pts;
     for (int h = 0; h < 2; ++h) {
         if ((e = cudaMalloc(&ctx->su[h], state * esz)) != cudaSuccess) return fail(e, "pr_create: alloc scratch u");

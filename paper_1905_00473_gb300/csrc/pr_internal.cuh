@@ -23,6 +23,10 @@ struct pr_ctx {
     double cmax = 0;
     void* kappa = nullptr;    // dtype, c^2 dt_f / dx^2
     double* cinv2 = nullptr;  // FP64 c^-2 (energy weights)
+    double* c64 = nullptr;    // FP64 c at the nodes of this grid
+    pr_options opts = {PR_F32, 4, 0, 1e-13, 0, 0};
+    pr_ctx* coarse = nullptr;         // the coarse propagator's context (C, Sec. 3.1)
+    struct pr_driver* drv = nullptr;  // Alg. 3 driver state (parareal.cu), lazily created
     // ping-pong state between passes, [N][pts] each: u, v (dtype), r (int8)
     void* su[2] = {nullptr, nullptr};
     void* sv[2] = {nullptr, nullptr};
@@ -38,6 +42,12 @@ struct pr_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
 };
+
+// ---- context construction / driver teardown ---------------------------------
+pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt, int m,
+                       double dt_c, int m_c, const pr_options& o, const std::vector<double>& c,
+                       pr_ctx** out);
+void pr_driver_free(pr_ctx* ctx);
 
 // ---- status helpers --------------------------------------------------------
 pr_status pr_fail(pr_ctx* ctx, pr_status st, const std::string& msg);
