@@ -135,15 +135,22 @@ enum { PR_CORR_PROCRUSTES = 0, PR_CORR_OMEGA1 = 1, PR_CORR_PLAIN = 2 };
 pr_status pr_coarse_sweep(pr_ctx* ctx, const void* u, const void* v, void* U_out, void* V_out,
                           int n_begin, int n_end, void* stream);
 
-/* pr_iterate -- the proposed method, Alg. 3, for K iterations.
+/* pr_iterate -- the proposed method, Alg. 3, for up to K iterations.
  *  u0, p0      initial state [n^d] (dtype, device).
- *  K           iterations (K = 0 returns the initial guess I C R u_{n-1}).
+ *  K           maximum iterations (K = 0 returns the initial guess I C R u_{n-1}).
  *  corrector   PR_CORR_*.
+ *  tol_err     with a reference: stop after the first iteration whose
+ *              relative energy-norm error at T is <= tol_err (Sec. 6).
+ *  u_ref, v_ref  reference state at T = N dt_com [n^d] (dtype, device), e.g.
+ *              the serial fine solution, or NULL (no error, no early stop).
  *  u_slices, v_slices  [N+1][n^d] (dtype, device): on return the states
- *              u^{K+1}_n, n = 0..N (u^{K+1}_0 = [u0, p0]).
+ *              u^{k+1}_n, n = 0..N, of the last iteration done (u^{k+1}_0 = [u0, p0]).
+ *  err_hist    HOST double[K] or NULL: sqrt(E(u^{k+1}_N - ref)/E(ref)), E the
+ *              discrete wave energy with the 4th-order nabla_h on the fine grid.
  *  resid_hist  HOST double[K] or NULL: ||F - Omega G||_F / ||F||_F of each
  *              iteration's data after the update (0 without Procrustes).
  *  rank_hist   HOST int[K] or NULL: retained singular values s.
+ *  k_done      HOST int or NULL: iterations done.
  * Fine sweeps run in the context dtype; Lambda, Omega, Lambda^dagger, I, the
  * data matrices and the SVD in FP64 (cuFFT, cuBLAS, cuSOLVER for the FFTs and
  * the dense factorisations).  The correction of a slice is applied to the
@@ -151,8 +158,9 @@ pr_status pr_coarse_sweep(pr_ctx* ctx, const void* u, const void* v, void* U_out
  * linearity equals Alg. 3's two applications.  Synchronises the stream.
  * Requires grad_order 2, 4, 6 or 8. */
 pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector,
-                     void* u_slices, void* v_slices, double* resid_hist, int* rank_hist,
-                     void* stream);
+                     double tol_err, const void* u_ref, const void* v_ref, void* u_slices,
+                     void* v_slices, double* err_hist, double* resid_hist, int* rank_hist,
+                     int* k_done, void* stream);
 
 /* pr_procrustes_correct -- UpdateSVD (Alg. 1): M <- M + F G^T with the
  * context's truncated SVD M = X Sigma Y^T (rank cut sigma_i/sigma_max > tol).

@@ -56,8 +56,10 @@ _SIGNATURES = {
                                                   ctypes.c_double, ctypes.c_int, _P, _P, _P, _P,
                                                   _P, ctypes.c_char_p, ctypes.c_size_t]),
     "pr_coarse_sweep": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
-    "pr_iterate": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P,
-                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _P]),
+    "pr_iterate": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P,
+                                  _P, _P, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int), _P]),
     "pr_procrustes_correct": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "pr_procrustes_apply": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "pr_procrustes_reset": (ctypes.c_int, [_P]),
@@ -245,17 +247,26 @@ def pr_coarse_sweep(ctx: Context, u, v, U_out, V_out, n_begin: int = 0,
     _check(st, ctx.handle)
 
 
-def pr_iterate(ctx: Context, u0, p0, K: int, corrector: int, u_slices, v_slices, stream=None):
-    """Runs Alg. 3; returns (residual history, rank history) as lists of length K."""
+def pr_iterate(ctx: Context, u0, p0, K: int, corrector: int, u_slices, v_slices,
+               u_ref=None, v_ref=None, tol_err: float = 0.0, stream=None) -> dict:
+    """Runs Alg. 3 for up to K iterations (early stop at tol_err with a reference);
+    returns {"k_done", "err", "residual", "rank"} histories."""
     pts = ctx.n ** ctx.dim
+    err = (ctypes.c_double * max(1, K))()
     res = (ctypes.c_double * max(1, K))()
     rk = (ctypes.c_int * max(1, K))()
+    kd = ctypes.c_int()
+    ur = ctx._arr(u_ref, "u_ref", pts) if u_ref is not None else None
+    vr = ctx._arr(v_ref, "v_ref", pts) if v_ref is not None else None
     st = load().pr_iterate(ctx.handle, ctx._arr(u0, "u0", pts), ctx._arr(p0, "p0", pts), K,
-                           corrector, ctx._arr(u_slices, "u_slices", (ctx.N + 1) * pts),
-                           ctx._arr(v_slices, "v_slices", (ctx.N + 1) * pts), res, rk,
-                           ctypes.c_void_p(_stream_ptr(stream)))
+                           corrector, tol_err, ur, vr,
+                           ctx._arr(u_slices, "u_slices", (ctx.N + 1) * pts),
+                           ctx._arr(v_slices, "v_slices", (ctx.N + 1) * pts), err, res, rk,
+                           ctypes.byref(kd), ctypes.c_void_p(_stream_ptr(stream)))
     _check(st, ctx.handle)
-    return list(res)[:K], list(rk)[:K]
+    k = kd.value
+    return {"k_done": k, "err": list(err)[:k] if ur is not None else [],
+            "residual": list(res)[:k], "rank": list(rk)[:k]}
 
 
 def pr_procrustes_correct(ctx: Context, Fcols, Gcols, stream=None) -> None:

@@ -238,6 +238,12 @@ __global__ void pair_to_complex(const double* __restrict__ a, const double* __re
     }
 }
 
+template <typename T>
+__global__ void diff_kernel(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ o, int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT)
+        o[j] = (T)((double)a[j] - (double)b[j]);
+}
+
 // ---------------------------------------------------------------- small dense helpers
 // R (n x n, upper) from a geqrf result (m x n, lda = m), zero below the diagonal
 __global__ void extract_r(const double* __restrict__ A, double* __restrict__ R, int64_t m, int n) {
@@ -293,6 +299,7 @@ struct pr_driver {
     double *UF = nullptr, *VG = nullptr, *A1 = nullptr, *A2 = nullptr, *H = nullptr;
     double *Xh = nullptr, *YhT = nullptr, *sig = nullptr, *work = nullptr, *rwork = nullptr;
     double *Xn = nullptr, *Yn = nullptr;
+    double *F2 = nullptr, *G2 = nullptr;            // copies of F, G for the residual
     int* info = nullptr;
     int64_t work_len = 0;
     int hcap = 0;   // allocated (s+N) capacity of the small matrices
@@ -312,7 +319,7 @@ void pr_driver_free(pr_ctx* ctx) {
     void* bufs[] = {d->vF_u, d->vF_v, d->Uc_u, d->Uc_v, d->w_u, d->w_v, d->Fm, d->Gm, d->dvec, d->gvec,
                     d->du, d->dut, d->zero, d->zc, d->zf, d->X, d->Y, d->S, d->QF, d->QG, d->RF, d->RG,
                     d->tau, d->UF, d->VG, d->A1, d->A2, d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork,
-                    d->Xn, d->Yn, d->info};
+                    d->Xn, d->Yn, d->F2, d->G2, d->info};
     for (void* b : bufs) cudaFree(b);
     delete d;
     ctx->drv = nullptr;
@@ -734,8 +741,9 @@ extern "C" pr_status pr_procrustes_reset(pr_ctx* ctx) {
 }
 
 extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector,
-                                void* u_slices, void* v_slices, double* resid_hist, int* rank_hist,
-                                void* stream) {
+                                double tol_err, const void* u_ref, const void* v_ref, void* u_slices,
+                                void* v_slices, double* err_hist, double* resid_hist, int* rank_hist,
+                                int* k_done, void* stream) {
     if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_iterate: ctx is NULL");
     if (!u0 || !p0 || !u_slices || !v_slices) return pr_fail(ctx, PR_EINVAL, "pr_iterate: NULL array");
     if (K < 0) return pr_fail(ctx, PR_EINVAL, "pr_iterate: K must be >= 0");
@@ -748,6 +756,10 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
     const size_t esz = ctx->dtype == PR_F32 ? 4 : 8;
     const int64_t pts = ctx->pts, cpts = d->cpts;
     const int N = ctx->N;
+    if (k_done) *k_done = 0;
+    // relative energy-norm error of u^{k+1}_N against the reference (Sec. 6)
+    double e_ref = 0.0;
+    if (u_ref && v_ref) PR_TRY_ST(pr_launch_energy(ctx, u_ref, v_ref, 1, &e_ref, st));
     char* us = (char*)u_slices;
     char* vs = (char*)v_slices;
     auto fu = [&](int n) { return us + (size_t)n * pts * esz; };
@@ -772,18 +784,15 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
             // F = [Lambda R v_n], G = [Lambda U_n]; UpdateSVD (Alg. 1)
             lambda_(ctx, d->vF_u, d->vF_v, d->Fm, ctx->ratio, ctx->n, pts, 1.0, N, d->rows, st);
             lambda_(ctx, d->Uc_u, d->Uc_v, d->Gm, 1, d->nc, cpts, 1.0, N, d->rows, st);
-            // the residual needs F, G after the update: keep copies in dvec-sized scratch
-            double* F2 = nullptr;
-            double* G2 = nullptr;
-            PR_TRY_ST(alloc(ctx, (void**)&F2, (size_t)d->rows * N * 8, "pr_iterate: alloc"));
-            PR_TRY_ST(alloc(ctx, (void**)&G2, (size_t)d->rows * N * 8, "pr_iterate: alloc"));
-            cudaMemcpyAsync(F2, d->Fm, (size_t)d->rows * N * 8, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(G2, d->Gm, (size_t)d->rows * N * 8, cudaMemcpyDeviceToDevice, st);
-            pr_status su = update_svd(ctx, d, d->Fm, d->Gm, N, st);
-            if (su == PR_OK) su = residual_(ctx, d, F2, G2, N, &res, st);
-            cudaFree(F2);
-            cudaFree(G2);
-            if (su != PR_OK) return su;
+            // the residual needs F, G after the update (update_svd consumes them)
+            if (!d->F2) {
+                PR_TRY_ST(alloc(ctx, (void**)&d->F2, (size_t)d->rows * N * 8, "pr_iterate: alloc"));
+                PR_TRY_ST(alloc(ctx, (void**)&d->G2, (size_t)d->rows * N * 8, "pr_iterate: alloc"));
+            }
+            cudaMemcpyAsync(d->F2, d->Fm, (size_t)d->rows * N * 8, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(d->G2, d->Gm, (size_t)d->rows * N * 8, cudaMemcpyDeviceToDevice, st);
+            PR_TRY_ST(update_svd(ctx, d, d->Fm, d->Gm, N, st));
+            PR_TRY_ST(residual_(ctx, d, d->F2, d->G2, N, &res, st));
         }
         // serial corrected sweep; u^{k+1}_0 = u^k_0 stays
         for (int n = 1; n <= N; ++n) {
@@ -810,6 +819,22 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
         }
         if (resid_hist) resid_hist[k - 1] = res;
         if (rank_hist) rank_hist[k - 1] = d->s;
+        if (k_done) *k_done = k;
+        if (u_ref && v_ref && e_ref > 0) {
+            // difference into the (now free) fine-sweep buffer, slice 0
+            if (ctx->dtype == PR_F32) {
+                diff_kernel<float><<<blocks_for(pts), kT, 0, st>>>((const float*)fu(N), (const float*)u_ref, (float*)d->vF_u, pts);
+                diff_kernel<float><<<blocks_for(pts), kT, 0, st>>>((const float*)fv(N), (const float*)v_ref, (float*)d->vF_v, pts);
+            } else {
+                diff_kernel<double><<<blocks_for(pts), kT, 0, st>>>((const double*)fu(N), (const double*)u_ref, (double*)d->vF_u, pts);
+                diff_kernel<double><<<blocks_for(pts), kT, 0, st>>>((const double*)fv(N), (const double*)v_ref, (double*)d->vF_v, pts);
+            }
+            double e = 0.0;
+            PR_TRY_ST(pr_launch_energy(ctx, d->vF_u, d->vF_v, 1, &e, st));
+            const double rel = sqrt(e / e_ref);
+            if (err_hist) err_hist[k - 1] = rel;
+            if (rel <= tol_err) break;
+        }
     }
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();

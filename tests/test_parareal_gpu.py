@@ -54,8 +54,8 @@ def _run(w, corrector, K, grad_order=4, tol=1e-13):
     p0 = torch.tensor(w.p0, dtype=dt, device="cuda")
     us = torch.zeros((w.n_slices + 1,) + w.shape, dtype=dt, device="cuda")
     vs = torch.zeros_like(us)
-    res, rk = binding.pr_iterate(ctx, u0, p0, K, CORR[corrector], us, vs)
-    return us.double().cpu().numpy(), vs.double().cpu().numpy(), res, rk
+    out = binding.pr_iterate(ctx, u0, p0, K, CORR[corrector], us, vs)
+    return us.double().cpu().numpy(), vs.double().cpu().numpy(), out["residual"], out["rank"]
 
 
 def test_coarse_sweep_matches_oracle(lib):
@@ -171,7 +171,36 @@ def test_papers_residual_table_on_gpu(lib):
                                 grad_order=order, tol=1e-14)
         us = torch.zeros((201, n), dtype=torch.float64, device="cuda")
         vs = torch.zeros_like(us)
-        res, rk = binding.pr_iterate(ctx, torch.tensor(u0, device="cuda"),
-                                     torch.zeros(n, dtype=torch.float64, device="cuda"), 3,
-                                     binding.PR_CORR_PROCRUSTES, us, vs)
+        res = binding.pr_iterate(ctx, torch.tensor(u0, device="cuda"),
+                                 torch.zeros(n, dtype=torch.float64, device="cuda"), 3,
+                                 binding.PR_CORR_PROCRUSTES, us, vs)["residual"]
         assert abs(np.mean(res) / golden["mean_relative_residual"][key] - 1) < 0.005, (key, res)
+
+
+def test_error_history_and_early_stop(lib):
+    """err_hist against a reference and the early stop at tol_err: with the
+    serial fine solution as reference the error at T reaches roundoff by
+    K = N (finite termination), so a loose tolerance stops earlier."""
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = _case(2, 64, 4, 12, "f64", 4)
+    ctx = _ctx(w, 4)
+    Pr = _problem(w, "procrustes")
+    ref = parareal.serial_fine(Pr, w.u0, w.p0)
+    dt = torch.float64
+    args = (torch.tensor(w.u0, dtype=dt, device="cuda"), torch.tensor(w.p0, dtype=dt, device="cuda"))
+    us = torch.zeros((5,) + w.shape, dtype=dt, device="cuda")
+    vs = torch.zeros_like(us)
+    ur = torch.tensor(ref[-1][0], dtype=dt, device="cuda")
+    vr = torch.tensor(ref[-1][1], dtype=dt, device="cuda")
+    out = binding.pr_iterate(ctx, *args, 4, binding.PR_CORR_PROCRUSTES, us, vs, ur, vr, 0.0)
+    assert out["k_done"] == 4 and len(out["err"]) == 4
+    recs = parareal.iterate(Pr, w.u0, w.p0, 4)
+    for k, rec in enumerate(recs):
+        e = energy.relative_energy_error(rec.states[-1][0], rec.states[-1][1], ref[-1][0], ref[-1][1],
+                                         w.c, w.dx_f)
+        assert abs(out["err"][k] - e) <= 1e-8 + 1e-6 * e, (k, out["err"][k], e)
+    assert out["err"][-1] < 1e-10
+    stop = binding.pr_iterate(ctx, *args, 4, binding.PR_CORR_PROCRUSTES, us, vs, ur, vr,
+                              out["err"][1] * 1.0001)
+    assert stop["k_done"] == 2
