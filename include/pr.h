@@ -179,6 +179,19 @@ pr_status pr_procrustes_apply(pr_ctx* ctx, const double* g, double* out, int* ra
 /* pr_procrustes_reset -- forget M (S empty, as at the start of Alg. 3). */
 pr_status pr_procrustes_reset(pr_ctx* ctx);
 
+/* pr_adjoint -- reverse mode through the serial fine solve F^N from (u0, p0)
+ * (N coupling intervals of m_F fine steps, Sec. 3.1 scheme).  For a loss L of
+ * the state at T with gradients (gu_T, gv_T) = (dL/du(T), dL/du_t(T)) it
+ * returns gu0 = dL/du0, gp0 = dL/dp0 and gc = dL/dc at the fine nodes (all
+ * [n^d], dtype, device).  Slice-start states are checkpointed and each slice
+ * is recomputed during the reverse sweep ((N+1) + (m_F+1) fields of context
+ * workspace); dL/dkappa accumulates in FP64.  The paper does not
+ * differentiate its method: at K = N iterations the parareal solution equals
+ * the serial fine solution (Alg. 3 terminates), so with the correctors frozen
+ * this is also its gradient.  Asynchronous on `stream`. */
+pr_status pr_adjoint(pr_ctx* ctx, const void* u0, const void* p0, const void* gu_T,
+                     const void* gv_T, void* gc, void* gu0, void* gp0, void* stream);
+
 /* pr_check -- synchronise `stream`, then report and clear a device-side error
  * flag set by a kernel whose bounded wait gave up (PR_ETIMEOUT), or a pending
  * CUDA error (PR_ECUDA). */

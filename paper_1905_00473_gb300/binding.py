@@ -63,6 +63,7 @@ _SIGNATURES = {
     "pr_procrustes_correct": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "pr_procrustes_apply": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "pr_procrustes_reset": (ctypes.c_int, [_P]),
+    "pr_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double)]),
@@ -294,3 +295,12 @@ def pr_procrustes_apply(ctx: Context, g=None, out=None, stream=None) -> int:
 
 def pr_procrustes_reset(ctx: Context) -> None:
     _check(load().pr_procrustes_reset(ctx.handle), ctx.handle)
+
+
+def pr_adjoint(ctx: Context, u0, p0, gu_T, gv_T, gc, gu0, gp0, stream=None) -> None:
+    """(dL/dc, dL/du0, dL/dp0) into gc, gu0, gp0 for the serial fine solve."""
+    pts = ctx.n ** ctx.dim
+    a = [ctx._arr(t, nm, pts) for t, nm in ((u0, "u0"), (p0, "p0"), (gu_T, "gu_T"), (gv_T, "gv_T"),
+                                           (gc, "gc"), (gu0, "gu0"), (gp0, "gp0"))]
+    st = load().pr_adjoint(ctx.handle, *a, ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, ctx.handle)

@@ -35,6 +35,8 @@ static void free_all(pr_ctx* c) {
         c->coarse = nullptr;
     }
     cudaFree(c->c64);
+    cudaFree(c->adj_ws);
+    c->adj_ws = nullptr;
     cudaFree(c->kappa);
     cudaFree(c->cinv2);
     for (int h = 0; h < 2; ++h) {
