@@ -60,7 +60,8 @@ typedef struct pr_grid {
 } pr_grid;
 
 /* Options.  block_depth: fine steps fused per HBM pass of the 2D FP32 kernel
- * (0 = library default; 1 = one step per pass).  Other fields are reserved
+ * (0 = library default 8; 8 or 4 use the fused kernel where it applies;
+ * 1 = one step per pass).  Other fields are reserved
  * for the coarse/correction stages and are ignored by the fine path. */
 typedef struct pr_options {
     int dtype;          /* pr_dtype */
@@ -191,6 +192,34 @@ pr_status pr_procrustes_reset(pr_ctx* ctx);
  * this is also its gradient.  Asynchronous on `stream`. */
 pr_status pr_adjoint(pr_ctx* ctx, const void* u0, const void* p0, const void* gu_T,
                      const void* gv_T, void* gc, void* gu0, void* gp0, void* stream);
+
+/* ---- batches of independent instances of uneven sizes ------------------- */
+typedef struct pr_batch pr_batch;
+
+/* pr_batch_create -- bind `count` instances (each its own context and its own
+ * [N_i][pts_i] input/output arrays, all on the current device) for one fine
+ * sweep each (Alg. 3 parallel phase, for every instance).
+ *  autotune   non-zero: for every instance time one sweep at each instantiated
+ *             block depth (8, 4 for the fused 2D kernel; 1 = one step per
+ *             pass) on `stream` and keep the fastest (written into the
+ *             instance's context); 0: keep each context's depth.
+ * Then captures all sweeps into one CUDA graph: one branch per instance,
+ * biggest first, spread over 8 library-owned streams between a fork and a
+ * join.  Runs (and synchronises) the timing sweeps; the bound arrays must
+ * stay valid until pr_batch_destroy.  The contexts must not be used
+ * concurrently with a launch of the batch. */
+pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void* const* u_in,
+                          const void* const* v_in, void* const* u_out, void* const* v_out,
+                          int autotune, void* stream, pr_batch** out);
+
+/* pr_batch_launch -- replay the captured graph on `stream` (asynchronous). */
+pr_status pr_batch_launch(pr_batch* b, void* stream);
+
+/* pr_batch_info -- chosen block depth and its timed sweep (ms) of instance i. */
+pr_status pr_batch_info(const pr_batch* b, int i, int* block_depth, double* tuned_ms);
+
+/* pr_batch_destroy -- free the graph and the streams (NULL is a no-op). */
+void pr_batch_destroy(pr_batch* b);
 
 /* pr_check -- synchronise `stream`, then report and clear a device-side error
  * flag set by a kernel whose bounded wait gave up (PR_ETIMEOUT), or a pending

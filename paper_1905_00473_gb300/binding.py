@@ -64,6 +64,12 @@ _SIGNATURES = {
     "pr_procrustes_apply": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "pr_procrustes_reset": (ctypes.c_int, [_P]),
     "pr_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "pr_batch_create": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int, _P,
+                                       ctypes.POINTER(_P)]),
+    "pr_batch_launch": (ctypes.c_int, [_P, _P]),
+    "pr_batch_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "pr_batch_destroy": (None, [_P]),
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double)]),
@@ -304,3 +310,36 @@ def pr_adjoint(ctx: Context, u0, p0, gu_T, gv_T, gc, gu0, gp0, stream=None) -> N
                                            (gc, "gc"), (gu0, "gu0"), (gp0, "gp0"))]
     st = load().pr_adjoint(ctx.handle, *a, ctypes.c_void_p(_stream_ptr(stream)))
     _check(st, ctx.handle)
+
+
+class Batch:
+    """A captured batch of fine sweeps over independent instances (pr_batch_*)."""
+
+    def __init__(self, ctxs, u_in, v_in, u_out, v_out, autotune=True, stream=None):
+        n = len(ctxs)
+        P = ctypes.c_void_p * n
+        self._keep = (list(ctxs), list(u_in), list(v_in), list(u_out), list(v_out))
+        arrs = [P(*[ctx._arr(t, name) for ctx, t in zip(ctxs, ts)])
+                for name, ts in (("u_in", u_in), ("v_in", v_in), ("u_out", u_out), ("v_out", v_out))]
+        out = ctypes.c_void_p()
+        st = load().pr_batch_create(n, P(*[c.handle for c in ctxs]), *arrs, 1 if autotune else 0,
+                                    ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
+        _check(st, None)
+        self.handle = out
+        self.count = n
+
+    def launch(self, stream=None):
+        _check(load().pr_batch_launch(self.handle, ctypes.c_void_p(_stream_ptr(stream))), None)
+
+    def info(self, i):
+        d, ms = ctypes.c_int(), ctypes.c_double()
+        _check(load().pr_batch_info(self.handle, i, ctypes.byref(d), ctypes.byref(ms)), None)
+        return d.value, ms.value
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().pr_batch_destroy(self.handle)
+                self.handle = ctypes.c_void_p(None)
+        except Exception:
+            pass

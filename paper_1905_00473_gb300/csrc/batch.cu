@@ -1,0 +1,182 @@
+// Batches of independent problem instances of uneven sizes (one parareal
+// iteration's fine sweep per instance, Alg. 3 parFor, for many instances):
+// per-instance block depth chosen by timing, then every instance's sweep
+// captured into one CUDA graph whose branches run on several streams.
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pr_internal.cuh"
+
+struct pr_batch {
+    std::vector<pr_ctx*> ctx;
+    std::vector<const void*> ui, vi;
+    std::vector<void*> uo, vo;
+    std::vector<int> depth;
+    std::vector<double> ms;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> ev;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string err;
+};
+
+namespace {
+
+constexpr int kStreams = 8;
+
+pr_status bfail(pr_batch* b, pr_status s, const std::string& m) {
+    if (b) b->err = m;
+    return pr_fail(nullptr, s, m);
+}
+
+void destroy(pr_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    delete b;
+}
+
+// time one sweep of instance i at depth d (after one warm-up sweep)
+pr_status time_depth(pr_batch* b, int i, int d, cudaStream_t st, double* ms) {
+    pr_ctx* c = b->ctx[i];
+    c->block_depth = d;
+    pr_status s = pr_fine_all_slices(c, b->ui[i], b->vi[i], b->uo[i], b->vo[i], 0, c->N, st);
+    if (s != PR_OK) return s;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    s = pr_fine_all_slices(c, b->ui[i], b->vi[i], b->uo[i], b->vo[i], 0, c->N, st);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != PR_OK) return s;
+    if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "pr_batch: timing");
+    *ms = t;
+    return PR_OK;
+}
+
+}  // namespace
+
+extern "C" pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void* const* u_in,
+                                     const void* const* v_in, void* const* u_out, void* const* v_out,
+                                     int autotune, void* stream, pr_batch** out) {
+    if (!out) return pr_fail(nullptr, PR_EINVAL, "pr_batch_create: out is NULL");
+    *out = nullptr;
+    if (count < 1 || !ctxs || !u_in || !v_in || !u_out || !v_out)
+        return pr_fail(nullptr, PR_EINVAL, "pr_batch_create: need count >= 1 and non-NULL arrays");
+    pr_batch* b = new pr_batch();
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i] || !u_in[i] || !v_in[i] || !u_out[i] || !v_out[i]) {
+            destroy(b);
+            return pr_fail(nullptr, PR_EINVAL, "pr_batch_create: NULL instance entry");
+        }
+        b->ctx.push_back(ctxs[i]);
+        b->ui.push_back(u_in[i]);
+        b->vi.push_back(v_in[i]);
+        b->uo.push_back(u_out[i]);
+        b->vo.push_back(v_out[i]);
+        b->depth.push_back(ctxs[i]->block_depth);
+        b->ms.push_back(0.0);
+    }
+    // autotuner: the fastest instantiated block depth per instance, timed once
+    if (autotune) {
+        for (int i = 0; i < count; ++i) {
+            double best = 1e300;
+            int best_d = 1;
+            for (int d : {8, 4, 1}) {
+                if (d > 1 && !pr_tb2d_supported(b->ctx[i], d)) continue;
+                double t = 0;
+                pr_status s = time_depth(b, i, d, st, &t);
+                if (s != PR_OK) {
+                    destroy(b);
+                    return s;
+                }
+                if (t < best) {
+                    best = t;
+                    best_d = d;
+                }
+            }
+            b->ctx[i]->block_depth = best_d;
+            b->depth[i] = best_d;
+            b->ms[i] = best;
+        }
+    }
+    // capture: fork on kStreams streams, one branch per instance, join
+    for (int k = 0; k < kStreams; ++k) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            destroy(b);
+            return pr_fail(nullptr, PR_ECUDA, "pr_batch_create: stream/event creation");
+        }
+        b->streams.push_back(s);
+        b->ev.push_back(e);
+    }
+    cudaEvent_t fork;
+    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    b->ev.push_back(fork);
+    cudaStream_t cap;
+    cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    b->streams.push_back(cap);
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        destroy(b);
+        return pr_cuda_fail(nullptr, e, "pr_batch_create: begin capture");
+    }
+    cudaEventRecord(fork, cap);
+    // biggest instances first, spread over the streams
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int c) {
+        return (double)b->ctx[a]->pts * b->ctx[a]->N * b->ctx[a]->m_f > (double)b->ctx[c]->pts * b->ctx[c]->N * b->ctx[c]->m_f;
+    });
+    for (int k = 0; k < kStreams; ++k) cudaStreamWaitEvent(b->streams[k], fork, 0);
+    pr_status ps = PR_OK;
+    for (int j = 0; j < count && ps == PR_OK; ++j) {
+        const int i = order[j];
+        ps = pr_fine_all_slices(b->ctx[i], b->ui[i], b->vi[i], b->uo[i], b->vo[i], 0, b->ctx[i]->N,
+                                b->streams[j % kStreams]);
+    }
+    for (int k = 0; k < kStreams; ++k) {
+        cudaEventRecord(b->ev[k], b->streams[k]);
+        cudaStreamWaitEvent(cap, b->ev[k], 0);
+    }
+    e = cudaStreamEndCapture(cap, &b->graph);
+    if (ps != PR_OK || e != cudaSuccess) {
+        destroy(b);
+        return ps != PR_OK ? ps : pr_cuda_fail(nullptr, e, "pr_batch_create: end capture");
+    }
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        destroy(b);
+        return pr_cuda_fail(nullptr, e, "pr_batch_create: instantiate");
+    }
+    *out = b;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_batch_launch(pr_batch* b, void* stream) {
+    if (!b || !b->exec) return pr_fail(nullptr, PR_EINVAL, "pr_batch_launch: no batch");
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "pr_batch_launch");
+    return PR_OK;
+}
+
+extern "C" pr_status pr_batch_info(const pr_batch* b, int i, int* block_depth, double* tuned_ms) {
+    if (!b || i < 0 || i >= (int)b->ctx.size()) return pr_fail(nullptr, PR_EINVAL, "pr_batch_info: bad index");
+    if (block_depth) *block_depth = b->depth[i];
+    if (tuned_ms) *tuned_ms = b->ms[i];
+    return PR_OK;
+}
+
+extern "C" void pr_batch_destroy(pr_batch* b) { destroy(b); }

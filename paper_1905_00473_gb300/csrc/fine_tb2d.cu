@@ -539,22 +539,30 @@ pr_status launch_depth(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     return mid ? launch_cfg<NT, B, true>(ctx, ps, st) : launch_cfg<NT, B, false>(ctx, ps, st);
 }
 
-constexpr int kDepth = 8;
+template <int B>
+pr_status launch_n(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
+    switch (ctx->n) {
+        case 256: return launch_depth<64, B>(ctx, ps, st);
+        case 512: return launch_depth<128, B>(ctx, ps, st);
+        case 1024: return launch_depth<256, B>(ctx, ps, st);
+        default: return pr_fail(ctx, PR_EINVAL, "tb2d: unsupported grid size");
+    }
+}
 
 }  // namespace
 
+// depths with an instantiated kernel: 8 (default) and 4 (smaller register and
+// shared-memory footprint; the batch autotuner chooses between them)
 bool pr_tb2d_supported(const pr_ctx* ctx, int depth) {
-    if (ctx->dim != 2 || ctx->dtype != PR_F32 || depth != kDepth) return false;
+    if (ctx->dim != 2 || ctx->dtype != PR_F32 || (depth != 8 && depth != 4)) return false;
     return ctx->n == 256 || ctx->n == 512 || ctx->n == 1024;
 }
 
 pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     if (ps.levels == 1) return pr_launch_fine_naive(ctx, ps, st);
-    if (ps.levels < 1 || ps.levels > kDepth) return pr_fail(ctx, PR_EINVAL, "tb2d: bad level count");
-    switch (ctx->n) {
-        case 256: return launch_depth<64, kDepth>(ctx, ps, st);
-        case 512: return launch_depth<128, kDepth>(ctx, ps, st);
-        case 1024: return launch_depth<256, kDepth>(ctx, ps, st);
-        default: return pr_fail(ctx, PR_EINVAL, "tb2d: unsupported grid size");
-    }
+    const int B = ctx->block_depth;
+    if (ps.levels < 1 || ps.levels > B) return pr_fail(ctx, PR_EINVAL, "tb2d: bad level count");
+    if (B == 8) return launch_n<8>(ctx, ps, st);
+    if (B == 4) return launch_n<4>(ctx, ps, st);
+    return pr_fail(ctx, PR_EINVAL, "tb2d: unsupported depth");
 }
