@@ -38,141 +38,44 @@
 // (half kick at g = m, no drift, fewer than B levels: the missing levels pass
 // rows through unchanged).
 #include "pr_internal.cuh"
+#include "tb_common.cuh"
 
 namespace {
+using namespace tb;
 
-constexpr int kCpt = 4;       // columns per thread
-constexpr int kPrefetch = 2;  // rows in flight ahead of the consumer
-constexpr int kRD = 16;       // kappa/D0 ring (power of two)
-constexpr int kRS = 5;        // u_hi, u_t, residual ring
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// bounded wait: false after `limit_ns` without completion
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                         uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
-        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
-        : "memory");
-}
-__device__ __forceinline__ uint64_t policy(int kind) {
-    uint64_t p;
-    if (kind == 0) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    else if (kind == 1) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    else asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-// Packed FP32 pairs (Blackwell f32x2 arithmetic): two lanes of one 64-bit
-// register, each lane rounded exactly like the scalar instruction.
-#ifndef PR_TB2D_PACKED
-#define PR_TB2D_PACKED 1
+#ifndef PR_TB2D_PREFETCH
+#define PR_TB2D_PREFETCH 2
 #endif
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t f2_pack(float a, float b) {
-    f2_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
+#ifndef PR_TB2D_RD
+#define PR_TB2D_RD 16   // kappa/D0 ring rows; 0 = the minimum B + prefetch + 1
+#endif
+constexpr int kCpt = 4;                     // columns per thread
+constexpr int kPrefetch = PR_TB2D_PREFETCH; // rows in flight ahead of the consumer
+constexpr int kRS = kPrefetch + 3;          // u_hi, u_t, residual ring
+// kappa/D0 ring for pipeline depth B: at least B + kPrefetch + 1 rows
+constexpr int rd_for(int B) {
+    return PR_TB2D_RD > B + kPrefetch + 1 ? PR_TB2D_RD : B + kPrefetch + 1;
 }
-__device__ __forceinline__ float f2_lo(f2_t x) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
-    return a;
-}
-__device__ __forceinline__ float f2_hi(f2_t x) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
-    return b;
-}
-__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
-    f2_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
-    f2_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
-struct Tb2dParams {
-    const float* u_in;
-    const float* v_in;
-    const int8_t* r_in;   // null: zero residual (first pass)
-    const float* kap;
-    float* u_out;
-    float* v_out;
-    int8_t* r_out;        // null: last pass, residual folded into u
-    int* flag;
-    int64_t rows_total;   // nslices * n
-    int n;
-    int g0, levels, m;
-    float dt;
-};
 
 template <int NT, int B>
 struct Smem {
+    static constexpr int RD = rd_for(B);
     static constexpr int W = NT * kCpt;                       // row width = n
     static constexpr size_t deep_row = (size_t)2 * W * 4;      // kappa, D0
     static constexpr size_t sh_row = (size_t)W * 4 * 2 + W;    // u_hi, u_t, residual
-    static constexpr size_t deep_bytes = kRD * deep_row;
+    static constexpr size_t deep_bytes = RD * deep_row;
     static constexpr size_t sh_bytes = kRS * sh_row;
     static constexpr size_t xbuf_bytes = (size_t)3 * B * 2 * NT * 4;  // [3][B][2][NT]
-    static constexpr size_t bar_bytes = (size_t)kRD * 8;
+    static constexpr size_t bar_bytes = (size_t)RD * 8;
     static constexpr size_t total = deep_bytes + sh_bytes + xbuf_bytes + bar_bytes;
-};
-
-// Per-segment constants of one CTA's current row range.
-struct Seg {
-    const float* u_s;
-    const float* v_s;
-    const int8_t* r_s;
-    int64_t slice_off;   // slice * n^2
-    uint32_t base;       // ring index of local row 0
-    int ylo;             // global row of local row 0
-    int H, L, nload;
 };
 
 template <int NT, int B>
 struct Shared {
-    unsigned char* deep;   // [kRD][kappa W | D0 W]
+    unsigned char* deep;   // [RD][kappa W | D0 W]
     unsigned char* shal;   // [kRS][u W | v W | r W]
     float* xbuf;           // [3][B][2][NT]: edge columns of each level's output row
-    uint64_t* bars;        // [kRD]
+    uint64_t* bars;        // [RD]
 };
 
 // One row iteration of the pipeline; PH = i mod 3 selects the register ring
@@ -188,6 +91,7 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
                                           uint64_t pol_last, uint64_t pol_norm) {
     using S = Smem<NT, B>;
     constexpr int W = S::W;
+    constexpr int kRD = S::RD;
     constexpr int CUR = PH, PRV = (PH + 2) % 3, NXT = (PH + 1) % 3;
     const int t = threadIdx.x;
     const int n = p.n;
@@ -200,8 +104,8 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
         const int rho = i + kPrefetch;
         const uint32_t qq = sg.base + (uint32_t)rho;
         const int64_t off = (int64_t)gy(rho) * n;
-        uint64_t* bar = &sh.bars[qq & (kRD - 1)];
-        unsigned char* drow = sh.deep + (size_t)(qq & (kRD - 1)) * S::deep_row;
+        uint64_t* bar = &sh.bars[qq % kRD];
+        unsigned char* drow = sh.deep + (size_t)(qq % kRD) * S::deep_row;
         unsigned char* srow = sh.shal + (size_t)(qq % kRS) * S::sh_row;
         const uint32_t row_bytes = (uint32_t)W * 4;
         mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)W : 0u));
@@ -225,7 +129,7 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
     float d0n[kCpt] = {0.f, 0.f, 0.f, 0.f};
     const bool have_row = i < sg.nload;
     if (have_row) {
-        if (!timed_out && !mbar_wait_bounded(&sh.bars[q & (kRD - 1)], (q / kRD) & 1u, 2000000000ull)) {
+        if (!timed_out && !mbar_wait_bounded(&sh.bars[q % kRD], (q / kRD) & 1u, 2000000000ull)) {
             atomicExch(p.flag, 1);
             timed_out = 1;
         }
@@ -270,7 +174,7 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
 #pragma unroll
     for (int l = 0; l < B; ++l) {
         const uint32_t qr = q - 1u - (uint32_t)l;
-        const float* drow = (const float*)(sh.deep + (size_t)(qr & (kRD - 1)) * S::deep_row);
+        const float* drow = (const float*)(sh.deep + (size_t)(qr % kRD) * S::deep_row);
         float vin[kCpt];
         if (l == 0) {
             const float4 v4 = *(const float4*)(sh.shal + (size_t)(qr % kRS) * S::sh_row + W * 4 + 16 * t);
@@ -387,7 +291,7 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
         }
     }
     if (have_row && i >= 1) {
-        float* dd = (float*)(sh.deep + (size_t)((q - 1) & (kRD - 1)) * S::deep_row) + W;
+        float* dd = (float*)(sh.deep + (size_t)((q - 1) % kRD) * S::deep_row) + W;
         *(float4*)(dd + kCpt * t) = make_float4(d0n[0], d0n[1], d0n[2], d0n[3]);
     }
     // one barrier per row; it also makes the abort decision uniform
@@ -397,6 +301,7 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
 template <int NT, int B, bool MID>
 __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     using S = Smem<NT, B>;
+    constexpr int kRD = S::RD;
     extern __shared__ __align__(128) unsigned char smem[];
     Shared<NT, B> sh;
     sh.deep = smem;
@@ -452,8 +357,8 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
                 int y = sg.ylo + rho;
                 if (y >= n) y -= n;
                 const int64_t off = (int64_t)y * n;
-                uint64_t* bar = &sh.bars[qq & (kRD - 1)];
-                unsigned char* drow = sh.deep + (size_t)(qq & (kRD - 1)) * S::deep_row;
+                uint64_t* bar = &sh.bars[qq % kRD];
+                unsigned char* drow = sh.deep + (size_t)(qq % kRD) * S::deep_row;
                 unsigned char* srow = sh.shal + (size_t)(qq % kRS) * S::sh_row;
                 const uint32_t row_bytes = (uint32_t)S::W * 4;
                 mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)S::W : 0u));
@@ -490,7 +395,7 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     if (aborted && t == 0) {
         // let copies still in flight land before the CTA's shared memory is released
         for (uint32_t q = consumed; q < issued; ++q)
-            (void)mbar_wait_bounded(&sh.bars[q & (kRD - 1)], (q / kRD) & 1u, 100000000ull);
+            (void)mbar_wait_bounded(&sh.bars[q % kRD], (q / kRD) & 1u, 100000000ull);
     }
 }
 
