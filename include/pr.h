@@ -43,7 +43,7 @@ typedef enum pr_status {
     PR_ENOMEM = 2,      /* device allocation failed */
     PR_ECUDA = 3,       /* a CUDA runtime call or a launch failed */
     PR_ETIMEOUT = 4,    /* a bounded device-side wait gave up (see pr_check) */
-    PR_EUNSTABLE = 5,   /* reserved: energy growth beyond the stability bound */
+    PR_EUNSTABLE = 5,   /* pr_iterate: the energy of the state at T is not finite */
     PR_ENOTCONV = 6     /* reserved: iteration did not reach its tolerance */
 } pr_status;
 
@@ -157,7 +157,9 @@ pr_status pr_coarse_sweep(pr_ctx* ctx, const void* u, const void* v, void* U_out
  * the dense factorisations).  The correction of a slice is applied to the
  * difference Lambda w - Lambda U_n with zero mode sum w - sum U_n, which by
  * linearity equals Alg. 3's two applications.  Synchronises the stream.
- * Requires grad_order 2, 4, 6 or 8. */
+ * Requires grad_order 2, 4, 6 or 8.  Returns PR_EUNSTABLE if the energy of
+ * the state at T stops being finite (the stability the method is built to
+ * keep, Sec. 5). */
 pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector,
                      double tol_err, const void* u_ref, const void* v_ref, void* u_slices,
                      void* v_slices, double* err_hist, double* resid_hist, int* rank_hist,
@@ -220,6 +222,15 @@ pr_status pr_batch_info(const pr_batch* b, int i, int* block_depth, double* tune
 
 /* pr_batch_destroy -- free the graph and the streams (NULL is a no-op). */
 void pr_batch_destroy(pr_batch* b);
+
+/* pr_debug_stall_waits -- test hook for the time-out path.  While enabled,
+ * fused-kernel launches of this context expect more bulk-copy bytes than
+ * they issue, so each bounded shared-memory barrier wait runs out (after
+ * 0.2 s instead of 2 s); the kernel records PR_ETIMEOUT, lets its copies
+ * land and returns, and later fused launches skip their work until
+ * pr_check reports and clears the error.  Nothing faults or hangs; results
+ * of the affected calls are not valid. */
+pr_status pr_debug_stall_waits(pr_ctx* ctx, int enable);
 
 /* pr_check -- synchronise `stream`, then report and clear a device-side error
  * flag set by a kernel whose bounded wait gave up (PR_ETIMEOUT), or a pending

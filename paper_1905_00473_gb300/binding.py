@@ -70,6 +70,7 @@ _SIGNATURES = {
     "pr_batch_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double)]),
     "pr_batch_destroy": (None, [_P]),
+    "pr_debug_stall_waits": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double)]),
@@ -343,3 +344,7 @@ class Batch:
                 self.handle = ctypes.c_void_p(None)
         except Exception:
             pass
+
+
+def pr_debug_stall_waits(ctx: Context, enable: bool) -> None:
+    _check(load().pr_debug_stall_waits(ctx.handle, 1 if enable else 0), ctx.handle)

@@ -820,6 +820,14 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
         if (resid_hist) resid_hist[k - 1] = res;
         if (rank_hist) rank_hist[k - 1] = d->s;
         if (k_done) *k_done = k;
+        // stability guard: the energy of the state at T must stay finite
+        double e_T = 0.0;
+        PR_TRY_ST(pr_launch_energy(ctx, fu(N), fv(N), 1, &e_T, st));
+        if (!isfinite(e_T)) {
+            char buf[96];
+            snprintf(buf, sizeof buf, "pr_iterate: energy at T is not finite after iteration %d", k);
+            return pr_fail(ctx, PR_EUNSTABLE, buf);
+        }
         if (u_ref && v_ref && e_ref > 0) {
             // difference into the (now free) fine-sweep buffer, slice 0
             if (ctx->dtype == PR_F32) {

@@ -370,6 +370,12 @@ extern "C" pr_status pr_fine_all_slices(pr_ctx* ctx, const void* u_in, const voi
     return s;
 }
 
+extern "C" pr_status pr_debug_stall_waits(pr_ctx* ctx, int enable) {
+    if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_debug_stall_waits: ctx is NULL");
+    ctx->debug_stall = enable != 0;
+    return PR_OK;
+}
+
 extern "C" pr_status pr_check(pr_ctx* ctx, void* stream) {
     if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_check: ctx is NULL");
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);

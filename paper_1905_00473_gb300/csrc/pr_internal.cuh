@@ -28,6 +28,7 @@ struct pr_ctx {
     pr_ctx* coarse = nullptr;         // the coarse propagator's context (C, Sec. 3.1)
     struct pr_driver* drv = nullptr;  // Alg. 3 driver state (parareal.cu), lazily created
     void* adj_ws = nullptr;           // pr_adjoint workspace (adjoint.cu), lazily created
+    int debug_stall = 0;              // pr_debug_stall_waits (tests of the time-out path)
     size_t adj_bytes = 0;
     // ping-pong state between passes, [N][pts] each: u, v (dtype), r (int8)
     void* su[2] = {nullptr, nullptr};

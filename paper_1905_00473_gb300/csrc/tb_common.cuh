@@ -103,6 +103,8 @@ struct Tb2dParams {
     int n;
     int g0, levels, m;
     float dt;
+    uint32_t tx_extra;    // test hook: bytes expected on top of those copied (0 normally)
+    uint64_t wait_ns;     // limit of each bounded mbarrier wait
 };
 
 // Per-segment constants of one CTA's current row range.

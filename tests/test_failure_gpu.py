@@ -1,0 +1,50 @@
+"""Failure detection without a GPU fault: a bounded wait that runs out is
+reported as PR_ETIMEOUT and leaves the context usable; a non-finite state is
+reported as PR_EUNSTABLE by the iteration's host-side guard."""
+import numpy as np
+import pytest
+
+from paper_1905_00473_gb300 import workloads as W
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_wait_times_out_and_context_recovers(lib):
+    import time
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = W.custom_case(2, 256, 2, 7, "f32", "smooth")     # one fused pass of 8 levels
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=1)
+    ud = torch.tensor(u, dtype=torch.float32, device="cuda")
+    vd = torch.tensor(v, dtype=torch.float32, device="cuda")
+    uo, vo = torch.zeros_like(ud), torch.zeros_like(vd)
+    binding.pr_debug_stall_waits(ctx, True)
+    t0 = time.time()
+    binding.pr_fine_all_slices(ctx, ud, vd, uo, vo)
+    with pytest.raises(binding.PrError) as ei:
+        binding.pr_check(ctx)
+    assert ei.value.status == 4 and "bounded wait" in str(ei.value)
+    assert time.time() - t0 < 30
+    binding.pr_check(ctx)                                 # flag cleared
+    binding.pr_debug_stall_waits(ctx, False)
+    ug, vg = P.run_gpu(ctx, u, v, "f32")
+    for s in range(2):
+        ur, vr = P.oracle_slice(w, u[s], v[s])
+        assert P.slice_errors(w, ug[s], vg[s], ur, vr)[0] <= P.TOL_ENERGY_F32
+
+
+def test_non_finite_state_is_reported_unstable(lib):
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = W.custom_case(2, 64, 3, 8, "f64", "smooth")
+    c = torch.tensor(w.c, device="cuda")
+    ctx = binding.pr_create(2, 64, 4, c, w.dt_f, w.dt_c, 3, w.t_final, dtype=binding.PR_F64)
+    u0 = torch.tensor(W.periodic_gaussian(2, 64, (0.5, 0.5), 0.1), device="cuda")
+    u0[3, 7] = float("nan")
+    us = torch.zeros((4, 64, 64), dtype=torch.float64, device="cuda")
+    vs = torch.zeros_like(us)
+    with pytest.raises(binding.PrError) as ei:
+        binding.pr_iterate(ctx, u0, torch.zeros_like(u0), 2, binding.PR_CORR_PLAIN, us, vs)
+    assert ei.value.status == 5
