@@ -162,7 +162,8 @@ def measured_peak() -> tuple[float, str]:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for rel in ("paper_1905_00473_gb300/csrc/fine_tb2d.cu", "paper_1905_00473_gb300/csrc/pr_internal.cuh"):
+    for rel in ("paper_1905_00473_gb300/csrc/fine_tb2d.cu", "paper_1905_00473_gb300/csrc/tb_common.cuh",
+                "paper_1905_00473_gb300/csrc/pr_internal.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -15,7 +15,7 @@
 // v_{n+1} = v_n + dt/2 (a_n + a_{n+1}), a = c^2 L u) with the two half kicks
 // of consecutive steps merged.
 //
-// FP32 keeps u as (u_hi, residual byte) between levels and evaluates
+// FP32 keeps u as (u_hi, rounding residual) between levels and evaluates
 // D(u_hi + du) as D(u_hi) + D(du), with D(u_hi) formed from differences
 // (u_nb - u_hi) so that the stencil of the O(1) field loses no bits to
 // cancellation; du starts at the decoded residual.
@@ -40,10 +40,11 @@ __device__ __forceinline__ void neighbours(int64_t p, int64_t n, int64_t* nb) {
     }
 }
 
-template <int DIM>
+// RT: the residual's storage type (int8_t byte or uint16_t bfloat16)
+template <int DIM, typename RT>
 __global__ void __launch_bounds__(256) level_f32(
-    const float* __restrict__ u, const int8_t* __restrict__ r, const float* __restrict__ v,
-    const float* __restrict__ kap, float* __restrict__ uo, int8_t* __restrict__ ro,
+    const float* __restrict__ u, const RT* __restrict__ r, const float* __restrict__ v,
+    const float* __restrict__ kap, float* __restrict__ uo, RT* __restrict__ ro,
     float* __restrict__ vo, int64_t n, int64_t pts, int64_t total, float wk, float dt, int drift) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -51,25 +52,25 @@ __global__ void __launch_bounds__(256) level_f32(
         const int64_t s = idx / pts;
         const int64_t p = idx - s * pts;
         const float* us = u + s * pts;
-        const int8_t* rs = r ? r + s * pts : nullptr;
+        const RT* rs = r ? r + s * pts : nullptr;
         int64_t nb[2 * DIM];
         neighbours<DIM>(p, n, nb);
         const float u0 = us[p];
-        float du = rs ? pr_resid_decode(rs[p], u0) : 0.0f;
+        float du = rs ? pr_resid_get(rs[p], u0) : 0.0f;
         float d0 = 0.0f, dn = 0.0f;
 #pragma unroll
         for (int k = 0; k < 2 * DIM; ++k) {
             const float ub = us[nb[k]];
             d0 += (ub - u0);
-            if (rs) dn += pr_resid_decode(rs[nb[k]], ub);
+            if (rs) dn += pr_resid_get(rs[nb[k]], ub);
         }
         const float lap = d0 + fmaf(-2.0f * DIM, du, dn);
         const float vn = fmaf(wk * kap[p], lap, v[idx]);
         if (drift) du = fmaf(dt, vn, du);
         vo[idx] = vn;
         if (ro) {
-            int8_t q;
-            uo[idx] = pr_sum_encode(u0, du, &q);
+            RT q;
+            uo[idx] = pr_resid_put(u0, du, &q);
             ro[idx] = q;
         } else {
             uo[idx] = u0 + du;
@@ -111,17 +112,24 @@ int grid_for(K kernel, int64_t total) {
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+template <int DIM, typename RT>
+void launch_f32(pr_ctx* ctx, const pr_pass& p, int64_t total, double wk, int drift, cudaStream_t st) {
+    auto k = level_f32<DIM, RT>;
+    k<<<grid_for(k, total), 256, 0, st>>>(
+        (const float*)p.u_in, (const RT*)p.r_in, (const float*)p.v_in, (const float*)ctx->kappa,
+        (float*)p.u_out, (RT*)p.r_out, (float*)p.v_out, ctx->n, ctx->pts, total, (float)wk,
+        (float)ctx->dt_f, drift);
+}
+
 template <int DIM>
 pr_status run_level(pr_ctx* ctx, const pr_pass& p, int g, const void* ui, const void* vi,
-                    const int8_t* ri, void* uo, void* vo, int8_t* ro, cudaStream_t st) {
+                    void* uo, void* vo, cudaStream_t st) {
     const int64_t total = (int64_t)p.nslices * ctx->pts;
     const int drift = g < p.m;
     const double wk = (g == 0 || g == p.m) ? 0.5 : 1.0;
     if (ctx->dtype == PR_F32) {
-        auto k = level_f32<DIM>;
-        k<<<grid_for(k, total), 256, 0, st>>>(
-            (const float*)ui, ri, (const float*)vi, (const float*)ctx->kappa, (float*)uo, ro,
-            (float*)vo, ctx->n, ctx->pts, total, (float)wk, (float)ctx->dt_f, drift);
+        if (p.rfmt == PR_RESID_BF16) launch_f32<DIM, uint16_t>(ctx, p, total, wk, drift, st);
+        else launch_f32<DIM, int8_t>(ctx, p, total, wk, drift, st);
     } else {
         auto k = level_f64<DIM>;
         k<<<grid_for(k, total), 256, 0, st>>>(
@@ -139,8 +147,8 @@ pr_status run_level(pr_ctx* ctx, const pr_pass& p, int g, const void* ui, const 
 pr_status pr_launch_fine_naive(pr_ctx* ctx, const pr_pass& p, cudaStream_t st) {
     if (p.levels != 1) return pr_fail(ctx, PR_EINVAL, "internal: naive pass must have one level");
     switch (ctx->dim) {
-        case 1: return run_level<1>(ctx, p, p.g0, p.u_in, p.v_in, p.r_in, p.u_out, p.v_out, p.r_out, st);
-        case 2: return run_level<2>(ctx, p, p.g0, p.u_in, p.v_in, p.r_in, p.u_out, p.v_out, p.r_out, st);
-        default: return run_level<3>(ctx, p, p.g0, p.u_in, p.v_in, p.r_in, p.u_out, p.v_out, p.r_out, st);
+        case 1: return run_level<1>(ctx, p, p.g0, p.u_in, p.v_in, p.u_out, p.v_out, st);
+        case 2: return run_level<2>(ctx, p, p.g0, p.u_in, p.v_in, p.u_out, p.v_out, st);
+        default: return run_level<3>(ctx, p, p.g0, p.u_in, p.v_in, p.u_out, p.v_out, st);
     }
 }

@@ -18,12 +18,13 @@
 // Loads.  One elected thread streams rows with cp.async.bulk (TMA bulk
 // copies: rows are contiguous and 16-byte aligned) into shared-memory rings
 // guarded by one mbarrier per row slot: kappa into a 16-row ring that also
-// holds D0 (below) for the rows in flight, u_hi, u_t and the residual byte
-// into a 5-row ring.  The finished row re-reads its u_hi from L2.  Waits are
+// holds D0 (below) for the rows in flight, u_hi, u_t and the bfloat16
+// residual into a 5-row ring.  The finished row re-reads its u_hi from L2.  Waits are
 // bounded: after ~2 s the CTA records PR_ETIMEOUT in a device flag and all
 // its threads leave the loop together.
 //
-// Precision.  Between passes u is (u_hi float, residual byte); inside a pass
+// Precision.  Between passes u is (u_hi float, bfloat16 rounding residual:
+// pr_internal.cuh); inside a pass
 // the state is du = u - u_hi with the stencil applied as
 // D(u) = D0 + D(du), D0 = D(u_hi) formed from differences once per pass.
 //
@@ -62,7 +63,7 @@ struct Smem {
     static constexpr int RD = rd_for(B);
     static constexpr int W = NT * kCpt;                       // row width = n
     static constexpr size_t deep_row = (size_t)2 * W * 4;      // kappa, D0
-    static constexpr size_t sh_row = (size_t)W * 4 * 2 + W;    // u_hi, u_t, residual
+    static constexpr size_t sh_row = (size_t)W * 4 * 2 + W * 2;  // u_hi, u_t, residual
     static constexpr size_t deep_bytes = RD * deep_row;
     static constexpr size_t sh_bytes = kRS * sh_row;
     static constexpr size_t xbuf_bytes = (size_t)3 * B * 2 * NT * 4;  // [3][B][2][NT]
@@ -73,7 +74,7 @@ struct Smem {
 template <int NT, int B>
 struct Shared {
     unsigned char* deep;   // [RD][kappa W | D0 W]
-    unsigned char* shal;   // [kRS][u W | v W | r W]
+    unsigned char* shal;   // [kRS][u W | v W | r 2W]
     float* xbuf;           // [3][B][2][NT]: edge columns of each level's output row
     uint64_t* bars;        // [RD]
 };
@@ -108,11 +109,11 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
         unsigned char* drow = sh.deep + (size_t)(qq % kRD) * S::deep_row;
         unsigned char* srow = sh.shal + (size_t)(qq % kRS) * S::sh_row;
         const uint32_t row_bytes = (uint32_t)W * 4;
-        mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)W : 0u) + p.tx_extra);
+        mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)W * 2 : 0u) + p.tx_extra);
         bulk_g2s(drow, p.kap + off, row_bytes, bar, pol_last);
         bulk_g2s(srow, sg.u_s + off, row_bytes, bar, pol_norm);
         bulk_g2s(srow + W * 4, sg.v_s + off, row_bytes, bar, pol_first);
-        if (sg.r_s) bulk_g2s(srow + W * 8, sg.r_s + off, (uint32_t)W, bar, pol_first);
+        if (sg.r_s) bulk_g2s(srow + W * 8, sg.r_s + off, (uint32_t)W * 2, bar, pol_first);
     }
 
     // ---- the finished row's u_hi, fetched early from L2 ------------------
@@ -138,10 +139,11 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
         const float4 u4 = *(const float4*)(s0 + 16 * t);
         const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
         if (sg.r_s) {
-            const char4 r4 = *(const char4*)(s0 + W * 8 + kCpt * t);
-            const int8_t rr[4] = {(int8_t)r4.x, (int8_t)r4.y, (int8_t)r4.z, (int8_t)r4.w};
-#pragma unroll
-            for (int k = 0; k < kCpt; ++k) R[0][NXT][k] = pr_resid_decode(rr[k], uu[k]);
+            const uint2 r2 = *(const uint2*)(s0 + W * 8 + 2 * kCpt * t);
+            R[0][NXT][0] = pr_bf16_lo(r2.x);
+            R[0][NXT][1] = pr_bf16_hi(r2.x);
+            R[0][NXT][2] = pr_bf16_lo(r2.y);
+            R[0][NXT][3] = pr_bf16_hi(r2.y);
         } else {
 #pragma unroll
             for (int k = 0; k < kCpt; ++k) R[0][NXT][k] = 0.0f;
@@ -269,10 +271,10 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
         const float u0[4] = {u0o.x, u0o.y, u0o.z, u0o.w};
         float uo[4];
         if (MID || p.r_out) {
-            int8_t qq[4];
+            float rr[4];
 #pragma unroll
-            for (int k = 0; k < kCpt; ++k) uo[k] = pr_sum_encode(u0[k], dout[k], &qq[k]);
-            *(char4*)(p.r_out + off_out) = make_char4(qq[0], qq[1], qq[2], qq[3]);
+            for (int k = 0; k < kCpt; ++k) uo[k] = pr_two_sum(u0[k], dout[k], &rr[k]);
+            *(uint2*)(p.r_out + off_out) = make_uint2(pr_bf16x2(rr[0], rr[1]), pr_bf16x2(rr[2], rr[3]));
         } else {
 #pragma unroll
             for (int k = 0; k < kCpt; ++k) uo[k] = u0[k] + dout[k];
@@ -364,11 +366,11 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
                 unsigned char* drow = sh.deep + (size_t)(qq % kRD) * S::deep_row;
                 unsigned char* srow = sh.shal + (size_t)(qq % kRS) * S::sh_row;
                 const uint32_t row_bytes = (uint32_t)S::W * 4;
-                mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)S::W : 0u) + p.tx_extra);
+                mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)S::W * 2 : 0u) + p.tx_extra);
                 bulk_g2s(drow, p.kap + off, row_bytes, bar, pol_last);
                 bulk_g2s(srow, sg.u_s + off, row_bytes, bar, pol_norm);
                 bulk_g2s(srow + S::W * 4, sg.v_s + off, row_bytes, bar, pol_first);
-                if (sg.r_s) bulk_g2s(srow + S::W * 8, sg.r_s + off, (uint32_t)S::W, bar, pol_first);
+                if (sg.r_s) bulk_g2s(srow + S::W * 8, sg.r_s + off, (uint32_t)S::W * 2, bar, pol_first);
             }
         }
         issued += (uint32_t)sg.nload;
@@ -421,11 +423,11 @@ pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     Tb2dParams p;
     p.u_in = (const float*)ps.u_in;
     p.v_in = (const float*)ps.v_in;
-    p.r_in = ps.r_in;
+    p.r_in = (const uint16_t*)ps.r_in;
     p.kap = (const float*)ctx->kappa;
     p.u_out = (float*)ps.u_out;
     p.v_out = (float*)ps.v_out;
-    p.r_out = ps.r_out;
+    p.r_out = (uint16_t*)ps.r_out;
     p.flag = ctx->dev_flag;
     p.rows_total = (int64_t)ps.nslices * ctx->n;
     p.n = (int)ctx->n;
@@ -470,6 +472,8 @@ bool pr_tb2d_supported(const pr_ctx* ctx, int depth) {
 
 pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     if (ps.levels == 1) return pr_launch_fine_naive(ctx, ps, st);
+    if ((ps.r_in || ps.r_out) && ps.rfmt != PR_RESID_BF16)
+        return pr_fail(ctx, PR_EINVAL, "tb2d: the fused pass carries a bfloat16 residual");
     const int B = ctx->block_depth;
     if (ps.levels < 1 || ps.levels > B) return pr_fail(ctx, PR_EINVAL, "tb2d: bad level count");
     if (B == 8) return launch_n<8>(ctx, ps, st);

@@ -265,10 +265,12 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
     if ((e = cudaMemcpy(ctx->c64, c.data(), pts * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "pr_create: upload c");
     const size_t state = (size_t)N * pts;
+    // the fused 2D sweeps carry a bfloat16 residual, one-level sweeps a byte
+    ctx->resid_bytes = o.dtype != PR_F32 ? 0 : (pr_tb2d_supported(ctx, 8) || pr_tb2d_supported(ctx, 4)) ? 2 : 1;
     for (int h = 0; h < 2; ++h) {
         if ((e = cudaMalloc(&ctx->su[h], state * esz)) != cudaSuccess) return fail(e, "pr_create: alloc scratch u");
         if ((e = cudaMalloc(&ctx->sv[h], state * esz)) != cudaSuccess) return fail(e, "pr_create: alloc scratch v");
-        if (o.dtype == PR_F32 && (e = cudaMalloc((void**)&ctx->sr[h], state)) != cudaSuccess)
+        if (ctx->resid_bytes && (e = cudaMalloc(&ctx->sr[h], state * ctx->resid_bytes)) != cudaSuccess)
             return fail(e, "pr_create: alloc scratch residual");
     }
     if ((e = cudaMalloc((void**)&ctx->dev_flag, sizeof(int))) != cudaSuccess) return fail(e, "pr_create: alloc flag");
@@ -318,18 +320,24 @@ extern "C" pr_status pr_fine_all_slices(pr_ctx* ctx, const void* u_in, const voi
             return pr_fail(ctx, PR_EINVAL, "pr_fine_all_slices: inputs and outputs overlap");
     }
     if (overlaps(uo, vo, bytes)) return pr_fail(ctx, PR_EINVAL, "pr_fine_all_slices: u_out and v_out overlap");
+    const int depth = ctx->block_depth;
+    const int rfmt = depth > 1 ? PR_RESID_BF16 : PR_RESID_I8;
+    const size_t rsz = rfmt == PR_RESID_BF16 ? 2 : 1;
+    if (ctx->dtype == PR_F32 && (size_t)ctx->resid_bytes < rsz)
+        return pr_fail(ctx, PR_EINVAL, "pr_fine_all_slices: residual scratch too small for the fused depth");
     cudaStream_t st = (cudaStream_t)stream;
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != ctx->device) cudaSetDevice(ctx->device);
 
     const int m = ctx->m_f;
-    const int depth = ctx->block_depth;
     const int levels_total = m + 1;            // m full steps = m + 1 kicks
     const int passes = (levels_total + depth - 1) / depth;
     auto scr_u = [&](int h) { return (char*)ctx->su[h] + off; };
     auto scr_v = [&](int h) { return (char*)ctx->sv[h] + off; };
-    auto scr_r = [&](int h) { return ctx->dtype == PR_F32 ? ctx->sr[h] + (size_t)n_begin * ctx->pts : nullptr; };
+    auto scr_r = [&](int h) -> void* {
+        return ctx->dtype == PR_F32 ? (char*)ctx->sr[h] + (size_t)n_begin * ctx->pts * rsz : nullptr;
+    };
     pr_status s = PR_OK;
     for (int p = 0; p < passes && s == PR_OK; ++p) {
         pr_pass ps;
@@ -337,6 +345,7 @@ extern "C" pr_status pr_fine_all_slices(pr_ctx* ctx, const void* u_in, const voi
         ps.g0 = p * depth;
         ps.levels = std::min(depth, levels_total - ps.g0);
         ps.m = m;
+        ps.rfmt = rfmt;
         const bool first = (p == 0), last = (p == passes - 1);
         ps.u_in = first ? (const void*)ui : scr_u((p - 1) & 1);
         ps.v_in = first ? (const void*)vi : scr_v((p - 1) & 1);

@@ -30,10 +30,12 @@ struct pr_ctx {
     void* adj_ws = nullptr;           // pr_adjoint workspace (adjoint.cu), lazily created
     int debug_stall = 0;              // pr_debug_stall_waits (tests of the time-out path)
     size_t adj_bytes = 0;
-    // ping-pong state between passes, [N][pts] each: u, v (dtype), r (int8)
+    // ping-pong state between passes, [N][pts] each: u, v (dtype), r (the
+    // residual: resid_bytes per point, 2 where a fused 2D sweep may run)
     void* su[2] = {nullptr, nullptr};
     void* sv[2] = {nullptr, nullptr};
-    int8_t* sr[2] = {nullptr, nullptr};
+    void* sr[2] = {nullptr, nullptr};
+    int resid_bytes = 0;
     double* partials = nullptr;     // energy partial sums
     int64_t partials_len = 0;
     int* dev_flag = nullptr;        // device-side error flag (bounded waits)
@@ -76,11 +78,17 @@ __device__ __forceinline__ uint32_t pr_resid_efield(float uhi) {
 __device__ __forceinline__ float pr_resid_decode(int8_t q, float uhi) {
     return (float)q * __uint_as_float(pr_resid_efield(uhi) - (31u << 23));
 }
-// Round u0 + du to float and encode the rounding error (TwoSum, Knuth).
+// s = fl(a + b) and the exact rounding error r = (a + b) - s (TwoSum, Knuth).
+__device__ __forceinline__ float pr_two_sum(float a, float b, float* r) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    *r = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+// Round u0 + du to float and encode the rounding error as the byte above.
 __device__ __forceinline__ float pr_sum_encode(float u0, float du, int8_t* q) {
-    const float s = __fadd_rn(u0, du);
-    const float bb = __fsub_rn(s, u0);
-    const float r = __fadd_rn(__fsub_rn(u0, __fsub_rn(s, bb)), __fsub_rn(du, bb));
+    float r;
+    const float s = pr_two_sum(u0, du, &r);
     const float inv = __uint_as_float((285u << 23) - pr_resid_efield(s));  // 2^(31-E)
     int qi;
     asm("cvt.rni.sat.s8.f32 %0, %1;" : "=r"(qi) : "f"(__fmul_rn(r, inv)));
@@ -88,16 +96,47 @@ __device__ __forceinline__ float pr_sum_encode(float u0, float du, int8_t* q) {
     return s;
 }
 
+// ---- the bfloat16 residual (sweeps with fused 2D passes) --------------------
+// The temporally blocked 2D kernel keeps r itself, rounded to bfloat16: the
+// float's exponent range with 8 significant bits, so |r - r_b| <= 2^-9 |r|
+// <= ulp(u_hi)/1024 (half the byte format's worst case) and no scale is
+// needed: decode is a shift, encode one convert per two values.  It costs a
+// second byte per point per pass, which the fused kernel (bound by issue, not
+// HBM) pays for with the instructions it saves; one-level sweeps, which are
+// HBM-bound, keep the byte.
+enum pr_resid_fmt { PR_RESID_I8 = 0, PR_RESID_BF16 = 1 };
+__device__ __forceinline__ float pr_bf16_decode(uint32_t h) { return __uint_as_float(h << 16); }
+// the two halves of a packed pair
+__device__ __forceinline__ float pr_bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float pr_bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+// two residuals packed as bf16 pairs: lo in bits 0..15, hi in 16..31
+__device__ __forceinline__ uint32_t pr_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+// overloads for kernels templated on the residual type
+__device__ __forceinline__ float pr_resid_get(int8_t q, float uhi) { return pr_resid_decode(q, uhi); }
+__device__ __forceinline__ float pr_resid_get(uint16_t h, float) { return pr_bf16_decode(h); }
+__device__ __forceinline__ float pr_resid_put(float u0, float du, int8_t* q) { return pr_sum_encode(u0, du, q); }
+__device__ __forceinline__ float pr_resid_put(float u0, float du, uint16_t* h) {
+    float r;
+    const float s = pr_two_sum(u0, du, &r);
+    *h = (uint16_t)pr_bf16x2(r, 0.0f);
+    return s;
+}
+
 // ---- kernels launched by the API -------------------------------------------
 struct pr_pass {
-    // state in: u (dtype), v (dtype), r (int8 or null = zero residual)
+    // state in: u (dtype), v (dtype), r (FP32 only; null = zero residual)
     const void* u_in;
     const void* v_in;
-    const int8_t* r_in;
+    const void* r_in;
     // state out: r_out null on the last pass (residual folded into u)
     void* u_out;
     void* v_out;
-    int8_t* r_out;
+    void* r_out;
+    int rfmt;             // pr_resid_fmt of r_in / r_out
     int nslices;          // slices in this launch (pointers already offset)
     int g0;               // global kick index of the first level
     int levels;           // kicks in this pass

@@ -93,11 +93,11 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
 struct Tb2dParams {
     const float* u_in;
     const float* v_in;
-    const int8_t* r_in;   // null: zero residual (first pass)
+    const uint16_t* r_in; // bfloat16 residual; null: zero residual (first pass)
     const float* kap;
     float* u_out;
     float* v_out;
-    int8_t* r_out;        // null: last pass, residual folded into u
+    uint16_t* r_out;      // null: last pass, residual folded into u
     int* flag;
     int64_t rows_total;   // nslices * n
     int n;
@@ -111,7 +111,7 @@ struct Tb2dParams {
 struct Seg {
     const float* u_s;
     const float* v_s;
-    const int8_t* r_s;
+    const uint16_t* r_s;
     int64_t slice_off;   // slice * n^2
     uint32_t base;       // ring index of local row 0
     int ylo;             // global row of local row 0
