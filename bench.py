@@ -312,7 +312,8 @@ def run_batch(a) -> int:
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"uneven batch: first {a.instances} seeded instances",
                        "instances": [{"n": w.n_fine, "N": w.n_slices, "m_f": w.m_f,
-                                      "depth": batch.info(i)[0]} for i, w in enumerate(ws)],
+                                      "depth": batch.info(i)[0], "columns": batch.info(i)[1]}
+                                     for i, w in enumerate(ws)],
                        "point_updates_per_step": units, "autotune_s": tune_s,
                        "graph": "one CUDA graph, 8 streams"}}
     print(json.dumps(line), flush=True)

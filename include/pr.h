@@ -60,8 +60,9 @@ typedef struct pr_grid {
 } pr_grid;
 
 /* Options.  block_depth: fine steps fused per HBM pass of the 2D FP32 kernel
- * (0 = library default 8; 8 or 4 use the fused kernel where it applies;
- * 1 = one step per pass).  Other fields are reserved
+ * (0 = library default: 8, or 4 where the width has no depth-8 kernel;
+ * 8 or 4 use the fused kernel where it applies: n = 256, 512, 1024, and
+ * 2048 at depth 4 only; 1 = one step per pass).  Other fields are reserved
  * for the coarse/correction stages and are ignored by the fine path. */
 typedef struct pr_options {
     int dtype;          /* pr_dtype */
@@ -202,9 +203,10 @@ typedef struct pr_batch pr_batch;
  * [N_i][pts_i] input/output arrays, all on the current device) for one fine
  * sweep each (Alg. 3 parallel phase, for every instance).
  *  autotune   non-zero: for every instance time one sweep at each instantiated
- *             block depth (8, 4 for the fused 2D kernel; 1 = one step per
+ *             fused configuration (block depth 8 or 4 with 2 or 4 columns
+ *             per thread for the fused 2D kernels; depth 1 = one step per
  *             pass) on `stream` and keep the fastest (written into the
- *             instance's context); 0: keep each context's depth.
+ *             instance's context); 0: keep each context's settings.
  * Then captures all sweeps into one CUDA graph: one branch per instance,
  * biggest first, spread over 8 library-owned streams between a fork and a
  * join.  Runs (and synchronises) the timing sweeps; the bound arrays must
@@ -217,11 +219,20 @@ pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void* const* u_i
 /* pr_batch_launch -- replay the captured graph on `stream` (asynchronous). */
 pr_status pr_batch_launch(pr_batch* b, void* stream);
 
-/* pr_batch_info -- chosen block depth and its timed sweep (ms) of instance i. */
-pr_status pr_batch_info(const pr_batch* b, int i, int* block_depth, double* tuned_ms);
+/* pr_batch_info -- chosen block depth, fused-kernel columns per thread (0 =
+ * chosen by width; see pr_set_fused_columns) and the timed sweep (ms) of
+ * instance i.  Any output pointer may be NULL. */
+pr_status pr_batch_info(const pr_batch* b, int i, int* block_depth, int* columns, double* tuned_ms);
 
 /* pr_batch_destroy -- free the graph and the streams (NULL is a no-op). */
 void pr_batch_destroy(pr_batch* b);
+
+/* pr_set_fused_columns -- thread geometry of the fused 2D FP32 passes of
+ * this context: 2 or 4 grid columns per thread (n/2 or n/4 threads per row),
+ * or 0 = by grid width (2 for n <= 512, 4 for n = 1024, the faster of the two
+ * on a GB300).  Both compute the same level recurrence; results agree to
+ * rounding.  PR_EINVAL for any other value.  Takes effect at the next call. */
+pr_status pr_set_fused_columns(pr_ctx* ctx, int columns);
 
 /* pr_debug_stall_waits -- test hook for the time-out path.  While enabled,
  * fused-kernel launches of this context expect more bulk-copy bytes than

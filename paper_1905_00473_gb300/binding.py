@@ -68,7 +68,8 @@ _SIGNATURES = {
                                        ctypes.POINTER(_P)]),
     "pr_batch_launch": (ctypes.c_int, [_P, _P]),
     "pr_batch_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                                     ctypes.POINTER(ctypes.c_double)]),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "pr_set_fused_columns": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_batch_destroy": (None, [_P]),
     "pr_debug_stall_waits": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -333,9 +334,11 @@ class Batch:
         _check(load().pr_batch_launch(self.handle, ctypes.c_void_p(_stream_ptr(stream))), None)
 
     def info(self, i):
-        d, ms = ctypes.c_int(), ctypes.c_double()
-        _check(load().pr_batch_info(self.handle, i, ctypes.byref(d), ctypes.byref(ms)), None)
-        return d.value, ms.value
+        """(block depth, fused columns per thread (0 = by width), tuned ms) of instance i."""
+        d, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(load().pr_batch_info(self.handle, i, ctypes.byref(d), ctypes.byref(c), ctypes.byref(ms)),
+               None)
+        return d.value, c.value, ms.value
 
     def __del__(self):
         try:
@@ -344,6 +347,11 @@ class Batch:
                 self.handle = ctypes.c_void_p(None)
         except Exception:
             pass
+
+
+def pr_set_fused_columns(ctx: Context, columns: int) -> None:
+    """Columns per thread of the fused 2D kernels: 2, 4 or 0 (by grid width)."""
+    _check(load().pr_set_fused_columns(ctx.handle, int(columns)), ctx.handle)
 
 
 def pr_debug_stall_waits(ctx: Context, enable: bool) -> None:

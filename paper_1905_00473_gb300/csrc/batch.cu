@@ -1,6 +1,7 @@
 // Batches of independent problem instances of uneven sizes (one parareal
 // iteration's fine sweep per instance, Alg. 3 parFor, for many instances):
-// per-instance block depth chosen by timing, then every instance's sweep
+// per-instance block depth and fused-kernel geometry chosen by timing, then
+// every instance's sweep
 // captured into one CUDA graph whose branches run on several streams.
 #include <stdio.h>
 
@@ -14,6 +15,7 @@ struct pr_batch {
     std::vector<const void*> ui, vi;
     std::vector<void*> uo, vo;
     std::vector<int> depth;
+    std::vector<int> cols;
     std::vector<double> ms;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> ev;
@@ -40,10 +42,12 @@ void destroy(pr_batch* b) {
     delete b;
 }
 
-// time one sweep of instance i at depth d (after one warm-up sweep)
-pr_status time_depth(pr_batch* b, int i, int d, cudaStream_t st, double* ms) {
+// time one sweep of instance i at depth d with cols columns per thread
+// (after one warm-up sweep)
+pr_status time_config(pr_batch* b, int i, int d, int cols, cudaStream_t st, double* ms) {
     pr_ctx* c = b->ctx[i];
     c->block_depth = d;
+    c->tb_cols = cols;
     pr_status s = pr_fine_all_slices(c, b->ui[i], b->vi[i], b->uo[i], b->vo[i], 0, c->N, st);
     if (s != PR_OK) return s;
     cudaEvent_t e0, e1;
@@ -85,17 +89,20 @@ extern "C" pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void*
         b->uo.push_back(u_out[i]);
         b->vo.push_back(v_out[i]);
         b->depth.push_back(ctxs[i]->block_depth);
+        b->cols.push_back(ctxs[i]->tb_cols);
         b->ms.push_back(0.0);
     }
-    // autotuner: the fastest instantiated block depth per instance, timed once
+    // autotuner: the fastest instantiated (depth, columns) per instance, timed once
     if (autotune) {
+        const int cands[5][2] = {{8, 4}, {8, 2}, {4, 4}, {4, 2}, {1, 0}};
         for (int i = 0; i < count; ++i) {
             double best = 1e300;
-            int best_d = 1;
-            for (int d : {8, 4, 1}) {
+            int best_d = 1, best_c = 0;
+            for (const auto& cd : cands) {
+                const int d = cd[0], cols = cd[1];
                 if (d > 1 && !pr_tb2d_supported(b->ctx[i], d)) continue;
                 double t = 0;
-                pr_status s = time_depth(b, i, d, st, &t);
+                pr_status s = time_config(b, i, d, cols, st, &t);
                 if (s != PR_OK) {
                     destroy(b);
                     return s;
@@ -103,10 +110,13 @@ extern "C" pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void*
                 if (t < best) {
                     best = t;
                     best_d = d;
+                    best_c = cols;
                 }
             }
             b->ctx[i]->block_depth = best_d;
+            b->ctx[i]->tb_cols = best_c;
             b->depth[i] = best_d;
+            b->cols[i] = best_c;
             b->ms[i] = best;
         }
     }
@@ -172,9 +182,11 @@ extern "C" pr_status pr_batch_launch(pr_batch* b, void* stream) {
     return PR_OK;
 }
 
-extern "C" pr_status pr_batch_info(const pr_batch* b, int i, int* block_depth, double* tuned_ms) {
+extern "C" pr_status pr_batch_info(const pr_batch* b, int i, int* block_depth, int* columns,
+                                   double* tuned_ms) {
     if (!b || i < 0 || i >= (int)b->ctx.size()) return pr_fail(nullptr, PR_EINVAL, "pr_batch_info: bad index");
     if (block_depth) *block_depth = b->depth[i];
+    if (columns) *columns = b->cols[i];
     if (tuned_ms) *tuned_ms = b->ms[i];
     return PR_OK;
 }

@@ -31,7 +31,8 @@
 // Work split.  The N*n rows of the batch are cut into one contiguous range
 // per CTA (persistent grid of #SM * occupancy CTAs); a range that crosses a
 // slice boundary is processed as separate segments, each with its own
-// L-row halo above and below (periodic in y).
+// L-row halo above and below (periodic in y), and the cut points balance
+// rows plus the halo and drain steps of every segment (balanced_row).
 //
 // Variants.  MID = a pass strictly inside the sweep (no half kick, every
 // level drifts, all B levels active), which is nearly every pass; the
@@ -60,8 +61,9 @@ constexpr int rd_for(int B) {
 
 template <int NT, int B>
 struct Smem {
-    static constexpr int RD = rd_for(B);
-    static constexpr int W = NT * kCpt;                       // row width = n
+    // wider CTAs (x-strips of 1040 columns) keep the minimum ring to fit
+    static constexpr int RD = NT > 256 ? B + kPrefetch + 1 : rd_for(B);
+    static constexpr int W = NT * kCpt;                       // columns held = n, or a strip
     static constexpr size_t deep_row = (size_t)2 * W * 4;      // kappa, D0
     static constexpr size_t sh_row = (size_t)W * 4 * 2 + W * 2;  // u_hi, u_t, residual
     static constexpr size_t deep_bytes = RD * deep_row;
@@ -79,50 +81,71 @@ struct Shared {
     uint64_t* bars;        // [RD]
 };
 
+template <int NT, int B>
+using Pos = RingPos<B, Smem<NT, B>::RD, (uint32_t)Smem<NT, B>::deep_row, kRS, (uint32_t)Smem<NT, B>::sh_row,
+                    kPrefetch>;
+
+// Request local row rho of the segment (kappa, u_hi, u_t, residual) into the
+// deep slot doff and the shallow slot soff; called by one thread.
+template <int NT, int B, int XH>
+__device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, const Shared<NT, B>& sh, int rho,
+                                          uint32_t doff, uint32_t soff, uint64_t pol_first, uint64_t pol_last,
+                                          uint64_t pol_norm) {
+    using S = Smem<NT, B>;
+    constexpr int W = S::W;
+    const int n = p.n;
+    const int64_t off = (int64_t)seg_row(sg.ylo, rho, n) * n;
+    uint64_t* bar = &sh.bars[doff / S::deep_row];
+    unsigned char* drow = sh.deep + doff;
+    unsigned char* srow = sh.shal + soff;
+    const uint32_t row_bytes = (uint32_t)W * 4;
+    mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)W * 2 : 0u) + p.tx_extra);
+    if (XH == 0) {
+        bulk_g2s(drow, p.kap + off, row_bytes, bar, pol_last);
+        bulk_g2s(srow, sg.u_s + off, row_bytes, bar, pol_norm);
+        bulk_g2s(srow + W * 4, sg.v_s + off, row_bytes, bar, pol_first);
+        if (sg.r_s) bulk_g2s(srow + W * 8, sg.r_s + off, (uint32_t)W * 2, bar, pol_first);
+    } else {
+        bulk_row_g2s(drow, p.kap + off, sg.x0, W, n, 4, bar, pol_last);
+        bulk_row_g2s(srow, sg.u_s + off, sg.x0, W, n, 4, bar, pol_norm);
+        bulk_row_g2s(srow + W * 4, sg.v_s + off, sg.x0, W, n, 4, bar, pol_first);
+        if (sg.r_s) bulk_row_g2s(srow + W * 8, sg.r_s + off, sg.x0, W, n, 2, bar, pol_first);
+    }
+}
+
 // One row iteration of the pipeline; PH = i mod 3 selects the register ring
 // slots and the xbuf buffer at compile time.  Register rings per level l:
 //   R[l][.]  du rows of level l's input: centre = slot PH, south = (PH+2)%3,
 //            north = (PH+1)%3 (written this iteration by the level below)
 //   VV[l][.] u_t of level l's input row: read (PH+2)%3, written PH
 // Returns true when some thread's bounded wait gave up.
-template <int NT, int B, bool MID, int PH>
+template <int NT, int B, int XH, bool MID, int PH>
 __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, const Shared<NT, B>& sh,
                                           int i, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
-                                          int& timed_out, uint32_t& consumed, uint64_t pol_first,
-                                          uint64_t pol_last, uint64_t pol_norm) {
+                                          Pos<NT, B>& ps, int& timed_out, uint32_t& consumed,
+                                          uint64_t pol_first, uint64_t pol_last, uint64_t pol_norm) {
     using S = Smem<NT, B>;
     constexpr int W = S::W;
-    constexpr int kRD = S::RD;
     constexpr int CUR = PH, PRV = (PH + 2) % 3, NXT = (PH + 1) % 3;
     const int t = threadIdx.x;
     const int n = p.n;
     const int L = MID ? B : sg.L;
     const uint32_t q = sg.base + (uint32_t)i;
-    auto gy = [&](int rho) { int y = sg.ylo + rho; return y >= n ? y - n : y; };
+    auto gy = [&](int rho) { return seg_row(sg.ylo, rho, n); };
 
     // ---- producer: row i + kPrefetch into the rings ---------------------
-    if (t == 0 && i + kPrefetch < sg.nload) {
-        const int rho = i + kPrefetch;
-        const uint32_t qq = sg.base + (uint32_t)rho;
-        const int64_t off = (int64_t)gy(rho) * n;
-        uint64_t* bar = &sh.bars[qq % kRD];
-        unsigned char* drow = sh.deep + (size_t)(qq % kRD) * S::deep_row;
-        unsigned char* srow = sh.shal + (size_t)(qq % kRS) * S::sh_row;
-        const uint32_t row_bytes = (uint32_t)W * 4;
-        mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)W * 2 : 0u) + p.tx_extra);
-        bulk_g2s(drow, p.kap + off, row_bytes, bar, pol_last);
-        bulk_g2s(srow, sg.u_s + off, row_bytes, bar, pol_norm);
-        bulk_g2s(srow + W * 4, sg.v_s + off, row_bytes, bar, pol_first);
-        if (sg.r_s) bulk_g2s(srow + W * 8, sg.r_s + off, (uint32_t)W * 2, bar, pol_first);
-    }
+    if (t == 0 && i + kPrefetch < sg.nload)
+        issue_row<NT, B, XH>(p, sg, sh, i + kPrefetch, ps.dn, ps.sn, pol_first, pol_last, pol_norm);
 
     // ---- the finished row's u_hi, fetched early from L2 ------------------
     const int rho_out = i - B;
-    const bool do_out = rho_out >= L && rho_out < L + sg.H;
+    // in an x-strip only the columns at least XH from both strip edges are final
+    const bool do_out = rho_out >= L && rho_out < L + sg.H &&
+                        (XH == 0 || (t >= XH / kCpt && t < NT - XH / kCpt));
     int64_t off_out = 0;
     float4 u0o = make_float4(0.f, 0.f, 0.f, 0.f);
     if (do_out) {
-        off_out = sg.slice_off + (int64_t)gy(rho_out) * n + kCpt * t;
+        off_out = sg.slice_off + (int64_t)gy(rho_out) * n + sg.x0 + kCpt * t;
         u0o = __ldcs((const float4*)(p.u_in + off_out));
     }
 
@@ -130,12 +153,12 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
     float d0n[kCpt] = {0.f, 0.f, 0.f, 0.f};
     const bool have_row = i < sg.nload;
     if (have_row) {
-        if (!timed_out && !mbar_wait_bounded(&sh.bars[q % kRD], (q / kRD) & 1u, p.wait_ns)) {
+        if (!timed_out && !mbar_wait_bounded(&sh.bars[ps.bar_of(ps.dq)], ps.dpar, p.wait_ns)) {
             atomicExch(p.flag, 1);
             timed_out = 1;
         }
         consumed = q + 1;
-        const unsigned char* s0 = sh.shal + (size_t)(q % kRS) * S::sh_row;
+        const unsigned char* s0 = sh.shal + ps.sq;
         const float4 u4 = *(const float4*)(s0 + 16 * t);
         const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
         if (sg.r_s) {
@@ -149,8 +172,8 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
             for (int k = 0; k < kCpt; ++k) R[0][NXT][k] = 0.0f;
         }
         if (i >= 1) {
-            const float* s1 = (const float*)(sh.shal + (size_t)((q - 1) % kRS) * S::sh_row);
-            const float* s2 = (const float*)(sh.shal + (size_t)((i >= 2 ? q - 2 : q - 1) % kRS) * S::sh_row);
+            const float* s1 = (const float*)(sh.shal + ps.s1);
+            const float* s2 = (const float*)(sh.shal + (i >= 2 ? ps.s2 : ps.s1));
             const float4 a = *(const float4*)(s1 + kCpt * t);
             const float4 b2 = *(const float4*)(s2 + kCpt * t);
             const float c[4] = {a.x, a.y, a.z, a.w};
@@ -175,11 +198,10 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
     float dout[kCpt], vout[kCpt];
 #pragma unroll
     for (int l = 0; l < B; ++l) {
-        const uint32_t qr = q - 1u - (uint32_t)l;
-        const float* drow = (const float*)(sh.deep + (size_t)(qr % kRD) * S::deep_row);
+        const float* drow = (const float*)(sh.deep + ps.lev[l]);
         float vin[kCpt];
         if (l == 0) {
-            const float4 v4 = *(const float4*)(sh.shal + (size_t)(qr % kRS) * S::sh_row + W * 4 + 16 * t);
+            const float4 v4 = *(const float4*)(sh.shal + ps.s1 + W * 4 + 16 * t);
             vin[0] = v4.x; vin[1] = v4.y; vin[2] = v4.z; vin[3] = v4.w;
         } else {
 #pragma unroll
@@ -293,14 +315,19 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
         }
     }
     if (have_row && i >= 1) {
-        float* dd = (float*)(sh.deep + (size_t)((q - 1) % kRD) * S::deep_row) + W;
+        float* dd = (float*)(sh.deep + ps.lev[0]) + W;
         *(float4*)(dd + kCpt * t) = make_float4(d0n[0], d0n[1], d0n[2], d0n[3]);
     }
+    ps.advance();
     // one barrier per row; it also makes the abort decision uniform
     return __syncthreads_or(timed_out) != 0;
 }
 
-template <int NT, int B, bool MID>
+// XH = 0: a CTA holds whole periodic rows (n = 4 NT).  XH > 0: it holds
+// x-strips of 4 NT columns, of which the middle 4 NT - 2 XH are final (the
+// stencil's reach grows one column per level, so XH >= B), and the rows of a
+// slice are covered by n / (4 NT - 2 XH) strips.
+template <int NT, int B, int XH, bool MID>
 __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     using S = Smem<NT, B>;
     constexpr int kRD = S::RD;
@@ -332,17 +359,23 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         pol_norm = policy(2);
     }
 
-    const int64_t r_begin = p.rows_total * blockIdx.x / gridDim.x;
-    const int64_t r_end = p.rows_total * (blockIdx.x + 1) / gridDim.x;
+    // per-CTA row ranges of equal cost: rows + (L + B) steps per segment
+    const int64_t r_begin = balanced_row(p.rows_total, n, L + B, blockIdx.x, gridDim.x);
+    const int64_t r_end = balanced_row(p.rows_total, n, L + B, blockIdx.x + 1, gridDim.x);
     uint32_t issued = 0, consumed = 0;
     int timed_out = 0;
     bool aborted = false;
 
+    // rows_total counts n rows per (slice, strip) pair
+    constexpr int kStripW = S::W - 2 * XH;
+    const int strips = XH ? n / kStripW : 1;
     for (int64_t seg0 = r_begin; seg0 < r_end && !aborted;) {
         Seg sg;
-        const int64_t slice = seg0 / n;
-        const int ya = (int)(seg0 - slice * n);
-        const int64_t seg1 = min(r_end, (slice + 1) * (int64_t)n);
+        const int64_t vslice = seg0 / n;
+        const int64_t slice = vslice / strips;
+        sg.x0 = XH ? (int)(vslice - slice * strips) * kStripW - XH : 0;
+        const int ya = (int)(seg0 - vslice * n);
+        const int64_t seg1 = min(r_end, (vslice + 1) * (int64_t)n);
         sg.H = (int)(seg1 - seg0);
         seg0 = seg1;
         sg.L = L;
@@ -359,21 +392,13 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         if (t == 0) {
             for (int rho = 0; rho < kPrefetch && rho < sg.nload; ++rho) {
                 const uint32_t qq = sg.base + (uint32_t)rho;
-                int y = sg.ylo + rho;
-                if (y >= n) y -= n;
-                const int64_t off = (int64_t)y * n;
-                uint64_t* bar = &sh.bars[qq % kRD];
-                unsigned char* drow = sh.deep + (size_t)(qq % kRD) * S::deep_row;
-                unsigned char* srow = sh.shal + (size_t)(qq % kRS) * S::sh_row;
-                const uint32_t row_bytes = (uint32_t)S::W * 4;
-                mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)S::W * 2 : 0u) + p.tx_extra);
-                bulk_g2s(drow, p.kap + off, row_bytes, bar, pol_last);
-                bulk_g2s(srow, sg.u_s + off, row_bytes, bar, pol_norm);
-                bulk_g2s(srow + S::W * 4, sg.v_s + off, row_bytes, bar, pol_first);
-                if (sg.r_s) bulk_g2s(srow + S::W * 8, sg.r_s + off, (uint32_t)S::W * 2, bar, pol_first);
+                issue_row<NT, B, XH>(p, sg, sh, rho, (qq % kRD) * (uint32_t)S::deep_row,
+                                     (qq % kRS) * (uint32_t)S::sh_row, pol_first, pol_last, pol_norm);
             }
         }
         issued += (uint32_t)sg.nload;
+        Pos<NT, B> ps;
+        ps.init(sg.base);
 
         float R[B][3][kCpt], VV[B][3][kCpt];
 #pragma unroll
@@ -385,17 +410,17 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
 
         int i = 0;
         for (; i + 3 <= niter; i += 3) {
-            if (tb2d_iter<NT, B, MID, 0>(p, sg, sh, i, R, VV, timed_out, consumed, pol_first, pol_last, pol_norm) ||
-                tb2d_iter<NT, B, MID, 1>(p, sg, sh, i + 1, R, VV, timed_out, consumed, pol_first, pol_last, pol_norm) ||
-                tb2d_iter<NT, B, MID, 2>(p, sg, sh, i + 2, R, VV, timed_out, consumed, pol_first, pol_last, pol_norm)) {
+            if (tb2d_iter<NT, B, XH, MID, 0>(p, sg, sh, i, R, VV, ps, timed_out, consumed, pol_first, pol_last, pol_norm) ||
+                tb2d_iter<NT, B, XH, MID, 1>(p, sg, sh, i + 1, R, VV, ps, timed_out, consumed, pol_first, pol_last, pol_norm) ||
+                tb2d_iter<NT, B, XH, MID, 2>(p, sg, sh, i + 2, R, VV, ps, timed_out, consumed, pol_first, pol_last, pol_norm)) {
                 aborted = true;
                 break;
             }
         }
         if (!aborted && i < niter)
-            aborted = tb2d_iter<NT, B, MID, 0>(p, sg, sh, i, R, VV, timed_out, consumed, pol_first, pol_last, pol_norm);
+            aborted = tb2d_iter<NT, B, XH, MID, 0>(p, sg, sh, i, R, VV, ps, timed_out, consumed, pol_first, pol_last, pol_norm);
         if (!aborted && i + 1 < niter)
-            aborted = tb2d_iter<NT, B, MID, 1>(p, sg, sh, i + 1, R, VV, timed_out, consumed, pol_first, pol_last, pol_norm);
+            aborted = tb2d_iter<NT, B, XH, MID, 1>(p, sg, sh, i + 1, R, VV, ps, timed_out, consumed, pol_first, pol_last, pol_norm);
     }
     if (aborted && t == 0) {
         // let copies still in flight land before the CTA's shared memory is released
@@ -404,10 +429,10 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     }
 }
 
-template <int NT, int B, bool MID>
+template <int NT, int B, int XH, bool MID>
 pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     using S = Smem<NT, B>;
-    auto kern = fine_tb2d_kernel<NT, B, MID>;
+    auto kern = fine_tb2d_kernel<NT, B, XH, MID>;
     static int configured_dev = -1;
     static int blocks_per_sm = 0;
     static int sms = 0;
@@ -429,7 +454,8 @@ pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     p.v_out = (float*)ps.v_out;
     p.r_out = (uint16_t*)ps.r_out;
     p.flag = ctx->dev_flag;
-    p.rows_total = (int64_t)ps.nslices * ctx->n;
+    const int strips = XH ? (int)ctx->n / (Smem<NT, B>::W - 2 * XH) : 1;
+    p.rows_total = (int64_t)ps.nslices * strips * ctx->n;
     p.n = (int)ctx->n;
     p.g0 = ps.g0;
     p.levels = ps.levels;
@@ -445,18 +471,24 @@ pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     return PR_OK;
 }
 
-template <int NT, int B>
+template <int NT, int B, int XH>
 pr_status launch_depth(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     const bool mid = ps.levels == B && ps.g0 >= 1 && ps.g0 + B - 1 < ps.m && ps.r_in && ps.r_out;
-    return mid ? launch_cfg<NT, B, true>(ctx, ps, st) : launch_cfg<NT, B, false>(ctx, ps, st);
+    return mid ? launch_cfg<NT, B, XH, true>(ctx, ps, st) : launch_cfg<NT, B, XH, false>(ctx, ps, st);
 }
 
 template <int B>
 pr_status launch_n(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     switch (ctx->n) {
-        case 256: return launch_depth<64, B>(ctx, ps, st);
-        case 512: return launch_depth<128, B>(ctx, ps, st);
-        case 1024: return launch_depth<256, B>(ctx, ps, st);
+        case 256: return launch_depth<64, B, 0>(ctx, ps, st);
+        case 512: return launch_depth<128, B, 0>(ctx, ps, st);
+        case 1024: return launch_depth<256, B, 0>(ctx, ps, st);
+        // two x-strips of 1040 columns (1024 final + 8 each side) per row; 260
+        // threads are 9 warps, 3 on one SM sub-partition, which caps a thread
+        // at 168 registers: depth 4 fits, depth 8 would spill
+        case 2048:
+            if constexpr (B == 4) return launch_depth<260, B, 8>(ctx, ps, st);
+            else return pr_fail(ctx, PR_EINVAL, "tb2d: n = 2048 runs at depth 4");
         default: return pr_fail(ctx, PR_EINVAL, "tb2d: unsupported grid size");
     }
 }
@@ -467,13 +499,21 @@ pr_status launch_n(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
 // shared-memory footprint; the batch autotuner chooses between them)
 bool pr_tb2d_supported(const pr_ctx* ctx, int depth) {
     if (ctx->dim != 2 || ctx->dtype != PR_F32 || (depth != 8 && depth != 4)) return false;
-    return ctx->n == 256 || ctx->n == 512 || ctx->n == 1024;
+    return ctx->n == 256 || ctx->n == 512 || ctx->n == 1024 || (ctx->n == 2048 && depth == 4);
 }
 
 pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     if (ps.levels == 1) return pr_launch_fine_naive(ctx, ps, st);
     if ((ps.r_in || ps.r_out) && ps.rfmt != PR_RESID_BF16)
         return pr_fail(ctx, PR_EINVAL, "tb2d: the fused pass carries a bfloat16 residual");
+    // Thread geometry (pr_set_fused_columns); by default two columns per thread
+    // (fine_tb2d_c2.cu) for n <= 512, where four columns leave too few warps
+    // per SM (n = 512: one CTA of 4 warps), and four (this file) for n = 1024,
+    // where 8 warps fill the SM and the x-neighbour exchange and per-row
+    // overhead are shared by twice the columns.
+    // n = 2048 runs in x-strips with four columns per thread whatever is set.
+    const int cols = ctx->tb_cols ? ctx->tb_cols : (ctx->n <= 512 ? 2 : 4);
+    if (cols == 2 && ctx->n <= 1024) return pr_launch_fine_tb2d_c2(ctx, ps, st);
     const int B = ctx->block_depth;
     if (ps.levels < 1 || ps.levels > B) return pr_fail(ctx, PR_EINVAL, "tb2d: bad level count");
     if (B == 8) return launch_n<8>(ctx, ps, st);

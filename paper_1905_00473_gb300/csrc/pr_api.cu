@@ -38,6 +38,7 @@ static void free_all(pr_ctx* c) {
     cudaFree(c->adj_ws);
     c->adj_ws = nullptr;
     cudaFree(c->kappa);
+    cudaFree(c->kappa_il);
     cudaFree(c->cinv2);
     for (int h = 0; h < 2; ++h) {
         cudaFree(c->su[h]);
@@ -236,8 +237,9 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
     ctx->m_c = m_c;
     ctx->cmax = cmax;
     ctx->opts = o;
+    // 0 = the deepest fused depth the geometry has (8, else 4), else one step per pass
     int depth = o.block_depth;
-    if (depth == 0) depth = 8;
+    if (depth == 0) depth = pr_tb2d_supported(ctx, 8) ? 8 : 4;
     ctx->block_depth = pr_tb2d_supported(ctx, depth) ? depth : 1;
 
     std::vector<char> kap(pts * esz);
@@ -262,6 +264,19 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
         return fail(e, "pr_create: upload kappa");
     if ((e = cudaMemcpy(ctx->cinv2, cinv2.data(), pts * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "pr_create: upload cinv2");
+    if ((pr_tb2d_supported(ctx, 8) || pr_tb2d_supported(ctx, 4)) && n <= 1024) {   // widths of the two-column kernel
+        // kappa for the two-column fused kernel: per thread (k(2t), k(2t+1), -, -),
+        // the free half filled with D0 in shared memory
+        std::vector<float> il((size_t)pts * 2, 0.0f);
+        const float* kf = (const float*)kap.data();
+        for (int64_t j = 0; j < pts / 2; ++j) {
+            il[4 * j] = kf[2 * j];
+            il[4 * j + 1] = kf[2 * j + 1];
+        }
+        if ((e = cudaMalloc((void**)&ctx->kappa_il, pts * 8)) != cudaSuccess) return fail(e, "pr_create: alloc kappa pairs");
+        if ((e = cudaMemcpy(ctx->kappa_il, il.data(), pts * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e, "pr_create: upload kappa pairs");
+    }
     if ((e = cudaMemcpy(ctx->c64, c.data(), pts * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "pr_create: upload c");
     const size_t state = (size_t)N * pts;
@@ -377,6 +392,14 @@ extern "C" pr_status pr_fine_all_slices(pr_ctx* ctx, const void* u_in, const voi
     }
     if (cur != ctx->device && cur >= 0) cudaSetDevice(cur);
     return s;
+}
+
+extern "C" pr_status pr_set_fused_columns(pr_ctx* ctx, int columns) {
+    if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_set_fused_columns: ctx is NULL");
+    if (columns != 0 && columns != 2 && columns != 4)
+        return pr_fail(ctx, PR_EINVAL, "pr_set_fused_columns: columns must be 0, 2 or 4");
+    ctx->tb_cols = columns;
+    return PR_OK;
 }
 
 extern "C" pr_status pr_debug_stall_waits(pr_ctx* ctx, int enable) {

@@ -20,8 +20,10 @@ struct pr_ctx {
     double T = 0, dt_com = 0, dt_f = 0, dt_c = 0, dx = 0;
     int m_f = 0, m_c = 0;
     int block_depth = 1;      // fine steps (kicks) per HBM pass
+    int tb_cols = 0;          // fused 2D kernel: columns per thread (0 = by width)
     double cmax = 0;
     void* kappa = nullptr;    // dtype, c^2 dt_f / dx^2
+    float* kappa_il = nullptr;  // 2D FP32: kappa per thread pair [y][x/2][k0 k1 0 0] (fine_tb2d_c2.cu)
     double* cinv2 = nullptr;  // FP64 c^-2 (energy weights)
     double* c64 = nullptr;    // FP64 c at the nodes of this grid
     pr_options opts = {PR_F32, 4, 0, 1e-13, 0, 0};
@@ -149,5 +151,7 @@ pr_status pr_launch_fine_naive(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
 // geometry is not supported (caller falls back to the naive path)
 bool pr_tb2d_supported(const pr_ctx* ctx, int depth);
 pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
+// the same passes with two columns per thread (16 warps per SM at n = 1024)
+pr_status pr_launch_fine_tb2d_c2(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
 pr_status pr_launch_energy(pr_ctx* ctx, const void* u, const void* v, int nslices,
                            double* e_host, cudaStream_t st);

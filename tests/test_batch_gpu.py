@@ -29,8 +29,10 @@ def test_batch_matches_oracle_after_autotune(lib):
         vo.append(torch.full_like(vi[-1], float("nan")))
     batch = binding.Batch(ctxs, ui, vi, uo, vo, autotune=True)
     depths = [batch.info(i)[0] for i in range(len(cases))]
+    cols = [batch.info(i)[1] for i in range(len(cases))]
     assert depths[3] == 1 and depths[4] == 1          # sizes without a fused kernel
     assert all(d in (4, 8) for d in depths[:3])
+    assert all(c in (2, 4) for c in cols[:3]) and cols[3] == 0 and cols[4] == 0
     for rep in range(2):
         for t in uo + vo:
             t.fill_(float("nan"))
@@ -45,10 +47,12 @@ def test_batch_matches_oracle_after_autotune(lib):
                 assert e <= P.TOL_ENERGY_F32, (rep, k, s, e)
 
 
-def test_depth4_kernel_matches_oracle(lib):
+@pytest.mark.parametrize("cols", [2, 4])
+def test_depth4_kernel_matches_oracle(lib, cols):
     w = W.custom_case(2, 512, 2, 21, "f32", "inclusion")
     ctx = P.make_ctx(w, block_depth=4)
     from paper_1905_00473_gb300 import binding
+    binding.pr_set_fused_columns(ctx, cols)
     assert binding.pr_info(ctx)["block_depth"] == 4
     u, v = W.slice_states(w, seed=7)
     ug, vg = P.run_gpu(ctx, u, v, "f32")

@@ -33,6 +33,7 @@ def _check_all(w, ctx, u, v, slices=None):
     return ug, vg, worst
 
 
+@pytest.mark.parametrize("cols", [2, 4])   # both fused kernels (pr_set_fused_columns)
 @pytest.mark.parametrize("n,m_f,N,medium", [
     (256, 20, 3, "inclusion"),   # passes of 8, 8, 5 levels; rows split across 3 slices
     (256, 7, 2, "smooth"),       # one full pass of 8 levels
@@ -40,13 +41,46 @@ def _check_all(w, ctx, u, v, slices=None):
     (512, 16, 2, "smooth"),      # 17 levels: 8, 8, then a one-level pass
     (1024, 12, 1, "inclusion"),  # widest tile, 13 levels
 ])
-def test_fused_2d_matches_oracle(lib, n, m_f, N, medium):
+def test_fused_2d_matches_oracle(lib, n, m_f, N, medium, cols):
     w = W.custom_case(2, n, N, m_f, "f32", medium)
     ctx = P.make_ctx(w)
     from paper_1905_00473_gb300 import binding
+    binding.pr_set_fused_columns(ctx, cols)
     assert binding.pr_info(ctx)["block_depth"] == 8
     u, v = W.slice_states(w, seed=1)
     _check_all(w, ctx, u, v)
+
+
+@pytest.mark.parametrize("m_f,N", [(9, 2), (4, 1)])
+def test_fused_2d_strips_2048(lib, m_f, N):
+    """n = 2048 runs in two x-strips of 1040 columns (8-column halo each side,
+    1024 final) at depth 4: passes of 4, 4, 2 levels (m_f = 9) or 4 + 1 levels
+    (m_f = 4), with rows of two slices and two strips split across the CTAs."""
+    w = W.custom_case(2, 2048, N, m_f, "f32", "inclusion")
+    ctx = P.make_ctx(w)
+    from paper_1905_00473_gb300 import binding
+    assert binding.pr_info(ctx)["block_depth"] == 4
+    u, v = W.slice_states(w, seed=11)
+    _check_all(w, ctx, u, v)
+
+
+@pytest.mark.parametrize("cols", [2, 4])
+@pytest.mark.parametrize("n,N", [(256, 1300), (512, 330)])
+def test_fused_2d_whole_slice_segments(lib, n, N, cols):
+    """So many slices that a CTA's row range holds whole slices: segments of
+    H = n rows whose halo rows wrap around the periodic slice on both sides
+    (row indices up to 2n + L).  Four distinct slice states are tiled over
+    the batch; the oracle checks the first, a middle and the last slices."""
+    w = W.custom_case(2, n, N, 9, "f32", "inclusion")   # 10 levels: 8 + 2
+    ctx = P.make_ctx(w)
+    from paper_1905_00473_gb300 import binding
+    binding.pr_set_fused_columns(ctx, cols)
+    w4 = W.custom_case(2, n, 4, 9, "f32", "inclusion")
+    u4, v4 = W.slice_states(w4, seed=7)
+    reps = (N + 3) // 4
+    u = np.ascontiguousarray(np.tile(u4, (reps, 1, 1))[:N])
+    v = np.ascontiguousarray(np.tile(v4, (reps, 1, 1))[:N])
+    _check_all(w, ctx, u, v, slices=[0, 1, N // 2, N - 1])
 
 
 @pytest.mark.parametrize("dim,n,m_f,N,dtype", [
@@ -124,6 +158,10 @@ def test_empty_range_and_invalid_arguments(lib):
     assert ei.value.status == 1
     with pytest.raises(binding.PrError):
         binding.pr_fine_all_slices(ctx, u, v, v, uo)       # output overlaps input
+    for bad in (1, 3, 8, -2):
+        with pytest.raises(binding.PrError) as ei:
+            binding.pr_set_fused_columns(ctx, bad)
+        assert ei.value.status == 1
     big = torch.zeros(4 * 256 * 256, device="cuda")
     with pytest.raises(binding.PrError):
         binding.pr_fine_all_slices(ctx, big[1:1 + 3 * 65536].view(3, 256, 256), v, uo, vo)  # unaligned
