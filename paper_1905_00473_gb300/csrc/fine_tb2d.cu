@@ -12,16 +12,25 @@
 // one kick+drift, and row i-B leaves the pipeline finished.  A level needs
 // its own column's rows above/below (registers) and the x-neighbours of its
 // edge columns, which come from the neighbouring threads through a small
-// double-buffered shared array written by the level below one iteration
+// triple-buffered shared array written by the level below one iteration
 // earlier.  One barrier per row.
 //
 // Loads.  One elected thread streams rows with cp.async.bulk (TMA bulk
 // copies: rows are contiguous and 16-byte aligned) into shared-memory rings
-// guarded by one mbarrier per row slot: kappa into a 16-row ring that also
+// guarded by one mbarrier per row slot: kappa into a 12-row ring that also
 // holds D0 (below) for the rows in flight, u_hi, u_t and the bfloat16
-// residual into a 5-row ring.  The finished row re-reads its u_hi from L2.  Waits are
-// bounded: after ~2 s the CTA records PR_ETIMEOUT in a device flag and all
-// its threads leave the loop together.
+// residual into a 6-row ring.  The finished row re-reads its u_hi from L2.
+// Waits are bounded: after ~2 s the CTA records PR_ETIMEOUT in a device flag
+// and all its threads leave the loop together.
+//
+// Static rings.  The row loop is unrolled 12-fold, the kappa/D0 ring depth,
+// which the shallow ring (6), the x-edge buffers (3) and the register rings
+// (3) divide.  Every segment starts at a ring position that is a multiple of
+// 12, so each unrolled step addresses its slots, mbarriers and buffers at
+// compile-time offsets; positions that receive no copy (drain steps, the
+// padding to the next multiple of 12) get a plain mbarrier arrival, so slot s
+// completes its j-th phase at position 12 j + s and the wait parity is the
+// parity of the ring lap.
 //
 // Precision.  Between passes u is (u_hi float, bfloat16 rounding residual:
 // pr_internal.cuh); inside a pass
@@ -45,97 +54,99 @@
 namespace {
 using namespace tb;
 
-#ifndef PR_TB2D_PREFETCH
-#define PR_TB2D_PREFETCH 2
-#endif
-#ifndef PR_TB2D_RD
-#define PR_TB2D_RD 16   // kappa/D0 ring rows; 0 = the minimum B + prefetch + 1
-#endif
-constexpr int kCpt = 4;                     // columns per thread
-constexpr int kPrefetch = PR_TB2D_PREFETCH; // rows in flight ahead of the consumer
-constexpr int kRS = kPrefetch + 3;          // u_hi, u_t, residual ring
-// kappa/D0 ring for pipeline depth B: at least B + kPrefetch + 1 rows
-constexpr int rd_for(int B) {
-    return PR_TB2D_RD > B + kPrefetch + 1 ? PR_TB2D_RD : B + kPrefetch + 1;
-}
+constexpr int kCpt = 4;   // columns per thread
+constexpr int kPre = 2;   // rows requested ahead of the consumer
+constexpr int kU = 12;    // loop unroll = rows of the kappa/D0 ring
+constexpr int kRS = 6;    // rows of the u_hi / u_t / residual ring
+static_assert(kU % 3 == 0 && kU % kRS == 0, "every ring period must divide the unroll");
+static_assert(kRS >= kPre + 3, "the shallow ring holds rows q-2 .. q+kPre");
 
+// Shared memory of one CTA.  Every ring slot, mbarrier and x-edge buffer of
+// the pipeline step that handles ring position q is (q mod its ring size), a
+// compile-time constant inside the kU-fold unrolled loop, because every
+// segment starts at a ring position that is a multiple of kU.
 template <int NT, int B>
 struct Smem {
-    // wider CTAs (x-strips of 1040 columns) keep the minimum ring to fit
-    static constexpr int RD = NT > 256 ? B + kPrefetch + 1 : rd_for(B);
-    static constexpr int W = NT * kCpt;                       // columns held = n, or a strip
-    static constexpr size_t deep_row = (size_t)2 * W * 4;      // kappa, D0
-    static constexpr size_t sh_row = (size_t)W * 4 * 2 + W * 2;  // u_hi, u_t, residual
-    static constexpr size_t deep_bytes = RD * deep_row;
-    static constexpr size_t sh_bytes = kRS * sh_row;
-    static constexpr size_t xbuf_bytes = (size_t)3 * B * 2 * NT * 4;  // [3][B][2][NT]
-    static constexpr size_t bar_bytes = (size_t)RD * 8;
-    static constexpr size_t total = deep_bytes + sh_bytes + xbuf_bytes + bar_bytes;
+    static_assert(kU >= B + kPre + 1, "the kappa/D0 ring holds rows q-B .. q+kPre");
+    static constexpr int W = NT * kCpt;                          // columns held: n, or an x-strip
+    static constexpr uint32_t deep_row = 2u * W * 4;             // kappa W | D0 W
+    static constexpr uint32_t sh_row = 10u * W;                  // u_hi W | u_t W (float) | r W (bf16)
+    static constexpr uint32_t deep_bytes = kU * deep_row;
+    static constexpr uint32_t sh_bytes = kRS * sh_row;
+    static constexpr uint32_t xbuf_bytes = 3u * B * 2 * NT * 4;  // [3][B][left|right][NT]
+    static constexpr uint32_t bar_bytes = kU * 8;
+    static constexpr uint32_t total = deep_bytes + sh_bytes + xbuf_bytes + bar_bytes;
+    static_assert(deep_row % 16 == 0 && sh_row % 16 == 0 && (W * 4) % 16 == 0,
+                  "bulk-copy destinations must stay 16-byte aligned");
+    __device__ static unsigned char* deep(unsigned char* sm, uint32_t slot) { return sm + slot * deep_row; }
+    __device__ static unsigned char* shal(unsigned char* sm, uint32_t slot) {
+        return sm + deep_bytes + slot * sh_row;
+    }
+    __device__ static float* xbuf(unsigned char* sm, uint32_t buf) {
+        return (float*)(sm + deep_bytes + sh_bytes) + buf * (B * 2 * NT);
+    }
+    __device__ static uint64_t* bar(unsigned char* sm, uint32_t slot) {
+        return (uint64_t*)(sm + deep_bytes + sh_bytes + xbuf_bytes) + slot;
+    }
 };
 
-template <int NT, int B>
-struct Shared {
-    unsigned char* deep;   // [RD][kappa W | D0 W]
-    unsigned char* shal;   // [kRS][u W | v W | r 2W]
-    float* xbuf;           // [3][B][2][NT]: edge columns of each level's output row
-    uint64_t* bars;        // [RD]
+struct Pols {
+    uint64_t first, last, norm;   // L2 evict-first (streamed), evict-last (kappa), normal (u_hi)
 };
-
-template <int NT, int B>
-using Pos = RingPos<B, Smem<NT, B>::RD, (uint32_t)Smem<NT, B>::deep_row, kRS, (uint32_t)Smem<NT, B>::sh_row,
-                    kPrefetch>;
 
 // Request local row rho of the segment (kappa, u_hi, u_t, residual) into the
-// deep slot doff and the shallow slot soff; called by one thread.
+// deep slot DS and the shallow slot SS; called by one thread.
 template <int NT, int B, int XH>
-__device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, const Shared<NT, B>& sh, int rho,
-                                          uint32_t doff, uint32_t soff, uint64_t pol_first, uint64_t pol_last,
-                                          uint64_t pol_norm) {
+__device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, unsigned char* sm, int rho,
+                                          uint32_t DS, uint32_t SS, const Pols& pol) {
     using S = Smem<NT, B>;
     constexpr int W = S::W;
     const int n = p.n;
     const int64_t off = (int64_t)seg_row(sg.ylo, rho, n) * n;
-    uint64_t* bar = &sh.bars[doff / S::deep_row];
-    unsigned char* drow = sh.deep + doff;
-    unsigned char* srow = sh.shal + soff;
-    const uint32_t row_bytes = (uint32_t)W * 4;
+    uint64_t* bar = S::bar(sm, DS);
+    unsigned char* drow = S::deep(sm, DS);
+    unsigned char* srow = S::shal(sm, SS);
+    constexpr uint32_t row_bytes = (uint32_t)W * 4;
     mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)W * 2 : 0u) + p.tx_extra);
     if (XH == 0) {
-        bulk_g2s(drow, p.kap + off, row_bytes, bar, pol_last);
-        bulk_g2s(srow, sg.u_s + off, row_bytes, bar, pol_norm);
-        bulk_g2s(srow + W * 4, sg.v_s + off, row_bytes, bar, pol_first);
-        if (sg.r_s) bulk_g2s(srow + W * 8, sg.r_s + off, (uint32_t)W * 2, bar, pol_first);
+        bulk_g2s(drow, p.kap + off, row_bytes, bar, pol.last);
+        bulk_g2s(srow, sg.u_s + off, row_bytes, bar, pol.norm);
+        bulk_g2s(srow + W * 4, sg.v_s + off, row_bytes, bar, pol.first);
+        if (sg.r_s) bulk_g2s(srow + W * 8, sg.r_s + off, (uint32_t)W * 2, bar, pol.first);
     } else {
-        bulk_row_g2s(drow, p.kap + off, sg.x0, W, n, 4, bar, pol_last);
-        bulk_row_g2s(srow, sg.u_s + off, sg.x0, W, n, 4, bar, pol_norm);
-        bulk_row_g2s(srow + W * 4, sg.v_s + off, sg.x0, W, n, 4, bar, pol_first);
-        if (sg.r_s) bulk_row_g2s(srow + W * 8, sg.r_s + off, sg.x0, W, n, 2, bar, pol_first);
+        bulk_row_g2s(drow, p.kap + off, sg.x0, W, n, 4, bar, pol.last);
+        bulk_row_g2s(srow, sg.u_s + off, sg.x0, W, n, 4, bar, pol.norm);
+        bulk_row_g2s(srow + W * 4, sg.v_s + off, sg.x0, W, n, 4, bar, pol.first);
+        if (sg.r_s) bulk_row_g2s(srow + W * 8, sg.r_s + off, sg.x0, W, n, 2, bar, pol.first);
     }
 }
 
-// One row iteration of the pipeline; PH = i mod 3 selects the register ring
-// slots and the xbuf buffer at compile time.  Register rings per level l:
-//   R[l][.]  du rows of level l's input: centre = slot PH, south = (PH+2)%3,
-//            north = (PH+1)%3 (written this iteration by the level below)
-//   VV[l][.] u_t of level l's input row: read (PH+2)%3, written PH
-// Returns true when some thread's bounded wait gave up.
-template <int NT, int B, int XH, bool MID, int PH>
-__device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, const Shared<NT, B>& sh,
-                                          int i, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
-                                          Pos<NT, B>& ps, int& timed_out, uint32_t& consumed,
-                                          uint64_t pol_first, uint64_t pol_last, uint64_t pol_norm) {
+// One pipeline step at ring position q = sg.base + i with K = q mod kU.
+// Register rings per level l (period 3, K mod 3 selects the slots):
+//   R[l][.]  du rows of level l's input: centre = K%3, south = (K+2)%3,
+//            north = (K+1)%3 (written this step by the level below)
+//   VV[l][.] u_t of level l's input row: read (K+2)%3, written K%3
+// `par` is the mbarrier phase parity of the current ring lap.  Returns true
+// when some thread's bounded wait gave up.
+template <int NT, int B, int XH, bool MID, int K>
+__device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, unsigned char* sm, int i,
+                                          uint32_t par, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
+                                          int& timed_out, uint32_t& consumed, uint32_t& issued_end,
+                                          const Pols& pol) {
     using S = Smem<NT, B>;
     constexpr int W = S::W;
-    constexpr int CUR = PH, PRV = (PH + 2) % 3, NXT = (PH + 1) % 3;
+    constexpr int CUR = K % 3, PRV = (K + 2) % 3, NXT = (K + 1) % 3;
+    constexpr uint32_t SQ = K % kRS, S1 = (K + kRS - 1) % kRS, S2 = (K + kRS - 2) % kRS;
+    constexpr uint32_t DN = (K + kPre) % kU, SN = (K + kPre) % kRS;
     const int t = threadIdx.x;
     const int n = p.n;
     const int L = MID ? B : sg.L;
-    const uint32_t q = sg.base + (uint32_t)i;
-    auto gy = [&](int rho) { return seg_row(sg.ylo, rho, n); };
 
-    // ---- producer: row i + kPrefetch into the rings ---------------------
-    if (t == 0 && i + kPrefetch < sg.nload)
-        issue_row<NT, B, XH>(p, sg, sh, i + kPrefetch, ps.dn, ps.sn, pol_first, pol_last, pol_norm);
+    // ---- producer: row i + kPre into the rings ---------------------------
+    if (t == 0 && i + kPre < sg.nload) {
+        issue_row<NT, B, XH>(p, sg, sm, i + kPre, DN, SN, pol);
+        issued_end = sg.base + (uint32_t)(i + kPre + 1);
+    }
 
     // ---- the finished row's u_hi, fetched early from L2 ------------------
     const int rho_out = i - B;
@@ -145,7 +156,7 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
     int64_t off_out = 0;
     float4 u0o = make_float4(0.f, 0.f, 0.f, 0.f);
     if (do_out) {
-        off_out = sg.slice_off + (int64_t)gy(rho_out) * n + sg.x0 + kCpt * t;
+        off_out = sg.slice_off + (int64_t)seg_row(sg.ylo, rho_out, n) * n + sg.x0 + kCpt * t;
         u0o = __ldcs((const float4*)(p.u_in + off_out));
     }
 
@@ -153,12 +164,12 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
     float d0n[kCpt] = {0.f, 0.f, 0.f, 0.f};
     const bool have_row = i < sg.nload;
     if (have_row) {
-        if (!timed_out && !mbar_wait_bounded(&sh.bars[ps.bar_of(ps.dq)], ps.dpar, p.wait_ns)) {
+        if (!timed_out && !mbar_wait_bounded(S::bar(sm, K), par, p.wait_ns)) {
             atomicExch(p.flag, 1);
             timed_out = 1;
         }
-        consumed = q + 1;
-        const unsigned char* s0 = sh.shal + ps.sq;
+        consumed = sg.base + (uint32_t)i + 1;
+        const unsigned char* s0 = S::shal(sm, SQ);
         const float4 u4 = *(const float4*)(s0 + 16 * t);
         const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
         if (sg.r_s) {
@@ -172,8 +183,10 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
             for (int k = 0; k < kCpt; ++k) R[0][NXT][k] = 0.0f;
         }
         if (i >= 1) {
-            const float* s1 = (const float*)(sh.shal + ps.s1);
-            const float* s2 = (const float*)(sh.shal + (i >= 2 ? ps.s2 : ps.s1));
+            // rows i-1 (centre) and i-2 (south; row i-1 again at i = 1, where
+            // the south row does not exist and D0 only feeds halo rows)
+            const float* s1 = (const float*)S::shal(sm, S1);
+            const float* s2 = (const float*)S::shal(sm, i >= 2 ? S2 : S1);
             const float4 a = *(const float4*)(s1 + kCpt * t);
             const float4 b2 = *(const float4*)(s2 + kCpt * t);
             const float c[4] = {a.x, a.y, a.z, a.w};
@@ -192,16 +205,16 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
     }
 
     // ---- levels: level l advances row i-1-l ------------------------------
-    const float* xr = sh.xbuf + (size_t)PRV * B * 2 * NT;
+    const float* xr = S::xbuf(sm, PRV);
     const int tl = (t + NT - 1) % NT, tr = (t + 1) % NT;
     const float dt = p.dt;
     float dout[kCpt], vout[kCpt];
 #pragma unroll
     for (int l = 0; l < B; ++l) {
-        const float* drow = (const float*)(sh.deep + ps.lev[l]);
+        const float* drow = (const float*)S::deep(sm, (uint32_t)((K + 2 * kU - 1 - l) % kU));
         float vin[kCpt];
         if (l == 0) {
-            const float4 v4 = *(const float4*)(sh.shal + ps.s1 + W * 4 + 16 * t);
+            const float4 v4 = *(const float4*)(S::shal(sm, S1) + W * 4 + 16 * t);
             vin[0] = v4.x; vin[1] = v4.y; vin[2] = v4.z; vin[3] = v4.w;
         } else {
 #pragma unroll
@@ -305,20 +318,19 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
         *(float4*)(p.v_out + off_out) = make_float4(vout[0], vout[1], vout[2], vout[3]);
     }
 
-    // ---- shared stores, read only in later iterations ----------------------
-    float* xw = sh.xbuf + (size_t)CUR * B * 2 * NT;
+    // ---- shared stores, read only in later steps ----------------------------
+    float* xw = S::xbuf(sm, CUR);
 #pragma unroll
     for (int l = 0; l < B; ++l) {
-        if (MID || l < L) {   // level l's input rows: edges read by level l next iteration
+        if (MID || l < L) {   // level l's input rows: edges read by level l next step
             xw[l * 2 * NT + t] = R[l][NXT][0];
             xw[l * 2 * NT + NT + t] = R[l][NXT][kCpt - 1];
         }
     }
     if (have_row && i >= 1) {
-        float* dd = (float*)(sh.deep + ps.lev[0]) + W;
+        float* dd = (float*)S::deep(sm, (uint32_t)((K + kU - 1) % kU)) + W;
         *(float4*)(dd + kCpt * t) = make_float4(d0n[0], d0n[1], d0n[2], d0n[3]);
     }
-    ps.advance();
     // one barrier per row; it also makes the abort decision uniform
     return __syncthreads_or(timed_out) != 0;
 }
@@ -330,13 +342,7 @@ __device__ __forceinline__ bool tb2d_iter(const Tb2dParams& p, const Seg& sg, co
 template <int NT, int B, int XH, bool MID>
 __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     using S = Smem<NT, B>;
-    constexpr int kRD = S::RD;
-    extern __shared__ __align__(128) unsigned char smem[];
-    Shared<NT, B> sh;
-    sh.deep = smem;
-    sh.shal = smem + S::deep_bytes;
-    sh.xbuf = (float*)(smem + S::deep_bytes + S::sh_bytes);
-    sh.bars = (uint64_t*)(smem + S::deep_bytes + S::sh_bytes + S::xbuf_bytes);
+    extern __shared__ __align__(128) unsigned char sm[];
 
     const int t = threadIdx.x;
     const int n = p.n;
@@ -347,22 +353,21 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     if (*(volatile int*)p.flag) return;
 
     if (t == 0) {
-        for (int s = 0; s < kRD; ++s) mbar_init(&sh.bars[s], 1);
+        for (int s = 0; s < kU; ++s) mbar_init(S::bar(sm, s), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    uint64_t pol_first = 0, pol_last = 0, pol_norm = 0;
-    if (t == 0) {
-        pol_first = policy(0);
-        pol_last = policy(1);
-        pol_norm = policy(2);
-    }
+    Pols pol = {0, 0, 0};
+    if (t == 0) pol = {policy(0), policy(1), policy(2)};
 
     // per-CTA row ranges of equal cost: rows + (L + B) steps per segment
     const int64_t r_begin = balanced_row(p.rows_total, n, L + B, blockIdx.x, gridDim.x);
     const int64_t r_end = balanced_row(p.rows_total, n, L + B, blockIdx.x + 1, gridDim.x);
-    uint32_t issued = 0, consumed = 0;
+    // ring positions: a segment occupies [base, base + niter) and the next one
+    // starts at the following multiple of kU; positions that receive no copy
+    // get a plain arrival, so slot s completes its phase j at position j kU + s
+    uint32_t pos = 0, consumed = 0, issued_end = 0;
     int timed_out = 0;
     bool aborted = false;
 
@@ -384,21 +389,17 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         sg.u_s = p.u_in + slice * pts;
         sg.v_s = p.v_in + slice * pts;
         sg.r_s = p.r_in ? p.r_in + slice * pts : nullptr;
-        sg.base = issued;
+        sg.base = pos;
         int ylo = (ya - L) % n;
         sg.ylo = ylo < 0 ? ylo + n : ylo;
         const int niter = sg.H + L + B;
 
         if (t == 0) {
-            for (int rho = 0; rho < kPrefetch && rho < sg.nload; ++rho) {
-                const uint32_t qq = sg.base + (uint32_t)rho;
-                issue_row<NT, B, XH>(p, sg, sh, rho, (qq % kRD) * (uint32_t)S::deep_row,
-                                     (qq % kRS) * (uint32_t)S::sh_row, pol_first, pol_last, pol_norm);
+            for (int rho = 0; rho < kPre && rho < sg.nload; ++rho) {
+                issue_row<NT, B, XH>(p, sg, sm, rho, (uint32_t)rho, (uint32_t)rho, pol);
+                issued_end = pos + (uint32_t)rho + 1;
             }
         }
-        issued += (uint32_t)sg.nload;
-        Pos<NT, B> ps;
-        ps.init(sg.base);
 
         float R[B][3][kCpt], VV[B][3][kCpt];
 #pragma unroll
@@ -408,24 +409,33 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
 #pragma unroll
                 for (int k = 0; k < kCpt; ++k) R[l][s][k] = VV[l][s][k] = 0.0f;
 
+        uint32_t par = (pos / kU) & 1u;
         int i = 0;
-        for (; i + 3 <= niter; i += 3) {
-            if (tb2d_iter<NT, B, XH, MID, 0>(p, sg, sh, i, R, VV, ps, timed_out, consumed, pol_first, pol_last, pol_norm) ||
-                tb2d_iter<NT, B, XH, MID, 1>(p, sg, sh, i + 1, R, VV, ps, timed_out, consumed, pol_first, pol_last, pol_norm) ||
-                tb2d_iter<NT, B, XH, MID, 2>(p, sg, sh, i + 2, R, VV, ps, timed_out, consumed, pol_first, pol_last, pol_norm)) {
-                aborted = true;
-                break;
-            }
+#define PR_TB2D_STEP(K)                                                                                   \
+    if (i >= niter) break;                                                                                 \
+    if (tb2d_step<NT, B, XH, MID, K>(p, sg, sm, i, par, R, VV, timed_out, consumed, issued_end, pol)) {   \
+        aborted = true;                                                                                    \
+        break;                                                                                             \
+    }                                                                                                      \
+    ++i;
+        for (;;) {
+            PR_TB2D_STEP(0) PR_TB2D_STEP(1) PR_TB2D_STEP(2) PR_TB2D_STEP(3)
+            PR_TB2D_STEP(4) PR_TB2D_STEP(5) PR_TB2D_STEP(6) PR_TB2D_STEP(7)
+            PR_TB2D_STEP(8) PR_TB2D_STEP(9) PR_TB2D_STEP(10) PR_TB2D_STEP(11)
+            par ^= 1u;
         }
-        if (!aborted && i < niter)
-            aborted = tb2d_iter<NT, B, XH, MID, 0>(p, sg, sh, i, R, VV, ps, timed_out, consumed, pol_first, pol_last, pol_norm);
-        if (!aborted && i + 1 < niter)
-            aborted = tb2d_iter<NT, B, XH, MID, 1>(p, sg, sh, i + 1, R, VV, ps, timed_out, consumed, pol_first, pol_last, pol_norm);
+#undef PR_TB2D_STEP
+        if (aborted) break;
+        // close the lap: complete the phases of the positions that got no copy
+        const uint32_t next = (pos + (uint32_t)niter + kU - 1) / kU * kU;
+        if (t == 0)
+            for (uint32_t q = pos + (uint32_t)sg.nload; q < next; ++q) mbar_arrive(S::bar(sm, q % kU));
+        pos = next;
     }
     if (aborted && t == 0) {
         // let copies still in flight land before the CTA's shared memory is released
-        for (uint32_t q = consumed; q < issued; ++q)
-            (void)mbar_wait_bounded(&sh.bars[q % kRD], (q / kRD) & 1u, p.wait_ns / 10);
+        for (uint32_t q = consumed; q < issued_end; ++q)
+            (void)mbar_wait_bounded(S::bar(sm, q % kU), (q / kU) & 1u, p.wait_ns / 10);
     }
 }
 
