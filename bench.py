@@ -309,11 +309,13 @@ def parareal_time_to_tol(dev, tol_err: float = 1e-4, k_max: int = 32, svd_tol: f
     out = binding.pr_iterate(ctx, u0, p0, k_max, binding.PR_CORR_PROCRUSTES, us, vs,
                              ref[N].contiguous(), refv[N].contiguous(), tol_err)
     t_par = 1e3 * (time.perf_counter() - t0)
+    phases = binding.pr_iterate_phases(ctx)
     reached = out["err"] and out["err"][-1] <= tol_err
     return {"workload": w.name, "corrector": "procrustes", "svd_tol": svd_tol, "tol_err": tol_err,
             "serial_fine_ms": t_serial, "parareal_ms": t_par, "iterations": out["k_done"],
             "reached": bool(reached),
             "speedup_vs_serial_fine": (t_serial / t_par) if reached else None,
+            "phases_ms": phases,
             "err_hist": out["err"], "rank_hist": out["rank"],
             "note": "pr_iterate wall time, host-synchronised, stopping at the first iteration "
                     "within tol_err of the serial fine solution computed by the same fine "

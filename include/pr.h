@@ -166,6 +166,16 @@ pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int K, int cor
                      void* v_slices, double* err_hist, double* resid_hist, int* rank_hist,
                      int* k_done, void* stream);
 
+/* pr_iterate_phases -- device time of the phases of the last pr_iterate call
+ * on this context, split like the per-phase columns of the paper's timing
+ * table (Sec. 7.2.4): ms[0] the initial serial coarse sweep u^1_n = I C R
+ * u^1_{n-1}; ms[1] the parallel computation (F and C R over all slices),
+ * ms[2] creating the corrector (Lambda of the data, UpdateSVD, residual) and
+ * ms[3] the serial corrected update, each summed over the iterations done.
+ *  ms   HOST double[4], written (zeros before the first pr_iterate).
+ * Timed with CUDA events on the call's stream.  PR_EINVAL for NULL pointers. */
+pr_status pr_iterate_phases(const pr_ctx* ctx, double* ms);
+
 /* pr_procrustes_correct -- UpdateSVD (Alg. 1): M <- M + F G^T with the
  * context's truncated SVD M = X Sigma Y^T (rank cut sigma_i/sigma_max > tol).
  *  Fcols, Gcols  DEVICE double [ncols][(d+1) n_c^d], one column per slice

@@ -60,6 +60,7 @@ _SIGNATURES = {
                                   _P, _P, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int), _P]),
+    "pr_iterate_phases": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "pr_procrustes_correct": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "pr_procrustes_apply": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "pr_procrustes_reset": (ctypes.c_int, [_P]),
@@ -276,6 +277,14 @@ def pr_iterate(ctx: Context, u0, p0, K: int, corrector: int, u_slices, v_slices,
     k = kd.value
     return {"k_done": k, "err": list(err)[:k] if ur is not None else [],
             "residual": list(res)[:k], "rank": list(rk)[:k]}
+
+
+def pr_iterate_phases(ctx: Context) -> dict:
+    """Device milliseconds of the last pr_iterate's phases (Sec. 7.2.4 table columns)."""
+    ms = (ctypes.c_double * 4)()
+    _check(load().pr_iterate_phases(ctx.handle, ms), ctx.handle)
+    return {"initial_coarse_ms": ms[0], "parallel_ms": ms[1], "corrector_ms": ms[2],
+            "serial_update_ms": ms[3]}
 
 
 def pr_procrustes_correct(ctx: Context, Fcols, Gcols, stream=None) -> None:

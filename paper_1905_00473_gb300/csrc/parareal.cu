@@ -303,6 +303,10 @@ struct pr_driver {
     int* info = nullptr;
     int64_t work_len = 0;
     int hcap = 0;   // allocated (s+N) capacity of the small matrices
+    // phase timers of the last pr_iterate (Sec. 7.2.4 table columns): initial
+    // coarse sweep, parallel computation, creating the corrector, serial update
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double phase_ms[4] = {0.0, 0.0, 0.0, 0.0};
 };
 
 void pr_driver_free(pr_ctx* ctx) {
@@ -316,6 +320,8 @@ void pr_driver_free(pr_ctx* ctx) {
     }
     if (d->blas) cublasDestroy(d->blas);
     if (d->sol) cusolverDnDestroy(d->sol);
+    for (cudaEvent_t e : d->ev)
+        if (e) cudaEventDestroy(e);
     void* bufs[] = {d->vF_u, d->vF_v, d->Uc_u, d->Uc_v, d->w_u, d->w_v, d->Fm, d->Gm, d->dvec, d->gvec,
                     d->du, d->dut, d->zero, d->zc, d->zf, d->X, d->Y, d->S, d->QF, d->QG, d->RF, d->RG,
                     d->tau, d->UF, d->VG, d->A1, d->A2, d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork,
@@ -753,6 +759,18 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
     pr_driver* d = nullptr;
     PR_TRY_ST(driver(ctx, st, &d));
     d->s = 0;   // a new run starts with an empty correlation matrix (Alg. 3)
+    for (int i = 0; i < 4; ++i) {
+        d->phase_ms[i] = 0.0;
+        if (!d->ev[i]) PR_CUDA_TRY(ctx, cudaEventCreate(&d->ev[i]));
+    }
+    // elapsed time between two recorded events, added to a phase total
+    auto add_phase = [&](int ph, int a, int b) -> pr_status {
+        float ms = 0.0f;
+        PR_CUDA_TRY(ctx, cudaEventSynchronize(d->ev[b]));
+        PR_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, d->ev[a], d->ev[b]));
+        d->phase_ms[ph] += ms;
+        return PR_OK;
+    };
     const size_t esz = ctx->dtype == PR_F32 ? 4 : 8;
     const int64_t pts = ctx->pts, cpts = d->cpts;
     const int N = ctx->N;
@@ -767,6 +785,7 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
     auto cu = [&](void* base, int n) { return (char*)base + (size_t)n * cpts * esz; };
 
     // Alg. 3 initialisation: u^1_0 = [u0, p0], u^1_n = I C R u^1_{n-1}
+    cudaEventRecord(d->ev[0], st);
     cudaMemcpyAsync(fu(0), u0, pts * esz, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(fv(0), p0, pts * esz, cudaMemcpyDeviceToDevice, st);
     for (int n = 1; n <= N; ++n) {
@@ -774,11 +793,15 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
         coarse_to_zc(ctx, d, d->w_u, d->w_v, nullptr, nullptr, st);
         PR_TRY_ST(interp_(ctx, d, nullptr, nullptr, fu(n), fv(n), st));
     }
+    cudaEventRecord(d->ev[1], st);
+    PR_TRY_ST(add_phase(0, 0, 1));
     for (int k = 1; k <= K; ++k) {
         // parallel phase: v_n = F u^k_{n-1}, U_n = C R u^k_{n-1}, n = 1..N
+        cudaEventRecord(d->ev[0], st);
         pr_status s = pr_fine_all_slices(ctx, fu(0), fv(0), d->vF_u, d->vF_v, 0, N, st);
         if (s != PR_OK) return s;
         PR_TRY_ST(coarse_of(ctx, fu(0), fv(0), d->Uc_u, d->Uc_v, N, st));
+        cudaEventRecord(d->ev[1], st);
         double res = 0.0;
         if (corrector == PR_CORR_PROCRUSTES) {
             // F = [Lambda R v_n], G = [Lambda U_n]; UpdateSVD (Alg. 1)
@@ -794,6 +817,7 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
             PR_TRY_ST(update_svd(ctx, d, d->Fm, d->Gm, N, st));
             PR_TRY_ST(residual_(ctx, d, d->F2, d->G2, N, &res, st));
         }
+        cudaEventRecord(d->ev[2], st);
         // serial corrected sweep; u^{k+1}_0 = u^k_0 stays
         for (int n = 1; n <= N; ++n) {
             PR_TRY_ST(coarse_of(ctx, fu(n - 1), fv(n - 1), d->w_u, d->w_v, 1, st));
@@ -817,6 +841,10 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
             const size_t vo = (size_t)(n - 1) * pts * esz;
             PR_TRY_ST(interp_(ctx, d, (char*)d->vF_u + vo, (char*)d->vF_v + vo, fu(n), fv(n), st));
         }
+        cudaEventRecord(d->ev[3], st);
+        PR_TRY_ST(add_phase(1, 0, 1));
+        PR_TRY_ST(add_phase(2, 1, 2));
+        PR_TRY_ST(add_phase(3, 2, 3));
         if (resid_hist) resid_hist[k - 1] = res;
         if (rank_hist) rank_hist[k - 1] = d->s;
         if (k_done) *k_done = k;
@@ -847,5 +875,11 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "pr_iterate");
+    return PR_OK;
+}
+
+extern "C" pr_status pr_iterate_phases(const pr_ctx* ctx, double* ms) {
+    if (!ctx || !ms) return PR_EINVAL;
+    for (int i = 0; i < 4; ++i) ms[i] = ctx->drv ? ctx->drv->phase_ms[i] : 0.0;
     return PR_OK;
 }

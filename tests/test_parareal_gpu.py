@@ -204,3 +204,31 @@ def test_error_history_and_early_stop(lib):
     stop = binding.pr_iterate(ctx, *args, 4, binding.PR_CORR_PROCRUSTES, us, vs, ur, vr,
                               out["err"][1] * 1.0001)
     assert stop["k_done"] == 2
+
+
+@pytest.mark.gpu
+def test_phase_timers_cover_the_call(lib):
+    """pr_iterate_phases: the four phase totals of the last call (Sec. 7.2.4
+    table columns) are non-negative, the parallel, corrector and serial phases
+    are non-zero once an iteration ran, and together they stay within the
+    call's wall time."""
+    import time
+
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = _case(2, 64, 4, 12, "f64", 4)
+    ctx = _ctx(w, 4)
+    dt = torch.float64
+    args = (torch.tensor(w.u0, dtype=dt, device="cuda"), torch.tensor(w.p0, dtype=dt, device="cuda"))
+    us = torch.zeros((5,) + w.shape, dtype=dt, device="cuda")
+    vs = torch.zeros_like(us)
+    assert all(v == 0.0 for v in binding.pr_iterate_phases(ctx).values())
+    binding.pr_iterate(ctx, *args, 1, binding.PR_CORR_PROCRUSTES, us, vs)   # library set-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    binding.pr_iterate(ctx, *args, 3, binding.PR_CORR_PROCRUSTES, us, vs)
+    wall_ms = 1e3 * (time.perf_counter() - t0)
+    ph = binding.pr_iterate_phases(ctx)
+    assert all(v >= 0.0 for v in ph.values()), ph
+    assert ph["parallel_ms"] > 0 and ph["corrector_ms"] > 0 and ph["serial_update_ms"] > 0, ph
+    assert sum(ph.values()) <= wall_ms * 1.05 + 0.5, (ph, wall_ms)
