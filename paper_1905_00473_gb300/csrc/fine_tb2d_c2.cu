@@ -15,8 +15,13 @@
 //   * kappa is stored pre-interleaved per thread (kappa0 kappa1 . .), so the
 //     TMA copy of a kappa row leaves room for D0 next to it and a level reads
 //     both with one 128-bit shared load.
-//   * the ring slots advance incrementally (no division by the ring sizes in
-//     the loop), and the per-level row offsets shift through registers.
+//   * static rings: the row loop is unrolled 12-fold, the depth of the
+//     kappa/D0 ring, which the u_hi/u_t/residual ring (6), the x-edge buffers
+//     (2) and the register rings (3) divide; every segment starts at a ring
+//     position that is a multiple of 12, so each unrolled step addresses its
+//     slots and mbarriers at compile-time offsets, and positions that get no
+//     copy receive a plain mbarrier arrival (the wait parity is the lap
+//     parity).
 //   * the x-neighbour edges go through a double-buffered shared array: with
 //     one barrier per row, a buffer written at row i is read at row i + 1 and
 //     rewritten at row i + 2, after the barrier that ends row i + 1.
@@ -30,14 +35,18 @@
 namespace {
 using namespace tb;
 
-constexpr int kC = 2;          // columns per thread
-constexpr int kPre = 2;        // rows requested ahead of the consumer
-constexpr int kRS = kPre + 3;  // u_hi / u_t / residual ring: rows q-2 .. q+kPre
+constexpr int kC = 2;     // columns per thread
+constexpr int kPre = 2;   // rows requested ahead of the consumer
+constexpr int kU = 12;    // loop unroll = rows of the kappa/D0 ring
+constexpr int kRS = 6;    // u_hi / u_t / residual ring: rows q-2 .. q+kPre
+static_assert(kU % 3 == 0 && kU % kRS == 0 && kU % 2 == 0, "every ring period must divide the unroll");
+static_assert(kRS >= kPre + 3, "the shallow ring holds rows q-2 .. q+kPre");
 
 template <int NT, int B>
 struct C2Smem {
+    static_assert(kU >= B + kPre + 1, "the kappa/D0 ring holds rows q-B .. q+kPre");
     static constexpr int W = NT * kC;                        // row width n
-    static constexpr int RD = B + kPre + 1;                  // kappa/D0 ring: rows q-B .. q+kPre
+    static constexpr int RD = kU;                            // kappa/D0 ring: rows q-B .. q+kPre
     static constexpr uint32_t deep_row = NT * 16;            // [t][kappa0 kappa1 D0_0 D0_1]
     static constexpr uint32_t sh_row = W * 10;               // u_hi W | u_t W (float) | r W (bf16)
     static constexpr uint32_t xbuf_floats = B * 2 * NT;      // one buffer: [B][left|right][NT]
@@ -58,9 +67,6 @@ struct C2Shared {
     uint64_t* bars;        // [RD], one per kappa/D0 slot, completes the row's copies
 };
 
-template <int NT, int B>
-using C2Pos = RingPos<B, C2Smem<NT, B>::RD, C2Smem<NT, B>::deep_row, kRS, C2Smem<NT, B>::sh_row, kPre>;
-
 // Request local row rho of the segment (kappa, u_hi, u_t, residual) into the
 // given slots; called by one thread.
 template <int NT, int B>
@@ -78,18 +84,25 @@ __device__ __forceinline__ void c2_issue(const Tb2dParams& p, const Seg& sg, con
     if (sg.r_s) bulk_g2s(sh.shal + soff + 8 * S::W, sg.r_s + off, 2u * S::W, bar, policy(0));
 }
 
-// One row of the pipeline; PH = i mod 3 names the register ring slots:
-//   R[l][.]  du rows of level l's input: centre PH, south (PH+2)%3, north
-//            (PH+1)%3 (written this row by the level below)
-//   VV[l][.] u_t of level l's input row: read (PH+2)%3, written PH
-// Returns true when some thread's bounded wait gave up.
-template <int NT, int B, bool MID, int PH>
+// One row of the pipeline at ring position q = sg.base + i, K = q mod 12;
+// K mod 3 names the register ring slots:
+//   R[l][.]  du rows of level l's input: centre K%3, south (K+2)%3, north
+//            (K+1)%3 (written this row by the level below)
+//   VV[l][.] u_t of level l's input row: read (K+2)%3, written K%3
+// `par` is the mbarrier phase parity of the current ring lap.  Returns true
+// when some thread's bounded wait gave up.
+template <int NT, int B, bool MID, int K>
 __device__ __forceinline__ bool c2_iter(const Tb2dParams& p, const Seg& sg, const C2Shared<NT, B>& sh,
-                                        int i, float (&R)[B][3][kC], float (&VV)[B][3][kC],
-                                        C2Pos<NT, B>& ps, int& timed_out, uint32_t& consumed) {
+                                        int i, uint32_t par, float (&R)[B][3][kC], float (&VV)[B][3][kC],
+                                        int& timed_out, uint32_t& consumed, uint32_t& issued_end) {
     using S = C2Smem<NT, B>;
     constexpr int W = S::W;
-    constexpr int CUR = PH, PRV = (PH + 2) % 3, NXT = (PH + 1) % 3;
+    constexpr int CUR = K % 3, PRV = (K + 2) % 3, NXT = (K + 1) % 3;
+    constexpr uint32_t SQ = (K % kRS) * S::sh_row, S1 = ((K + kRS - 1) % kRS) * S::sh_row,
+                       S2 = ((K + kRS - 2) % kRS) * S::sh_row;
+    constexpr uint32_t DN = ((K + kPre) % kU) * S::deep_row, SN = ((K + kPre) % kRS) * S::sh_row;
+    // deep slot of the row at offset c from position q
+    auto dslot = [](int c) { return (uint32_t)(((K + c + 2 * kU) % kU) * S::deep_row); };
     const int t = threadIdx.x;
     const int n = p.n;
     const int L = MID ? B : sg.L;
@@ -97,7 +110,10 @@ __device__ __forceinline__ bool c2_iter(const Tb2dParams& p, const Seg& sg, cons
     auto gy = [&](int rho) { return seg_row(sg.ylo, rho, n); };
 
     // ---- producer: row i + kPre ---------------------------------------------
-    if (t == 0 && i + kPre < sg.nload) c2_issue<NT, B>(p, sg, sh, i + kPre, ps.dn, ps.sn);
+    if (t == 0 && i + kPre < sg.nload) {
+        c2_issue<NT, B>(p, sg, sh, i + kPre, DN, SN);
+        issued_end = sg.base + (uint32_t)(i + kPre + 1);
+    }
 
     // ---- the finished row's u_hi, fetched early from L2 ----------------------
     const int rho_out = i - B;
@@ -113,12 +129,12 @@ __device__ __forceinline__ bool c2_iter(const Tb2dParams& p, const Seg& sg, cons
     float d0n[kC] = {0.f, 0.f};
     const bool have_row = i < sg.nload;
     if (have_row) {
-        if (!timed_out && !mbar_wait_bounded(&sh.bars[ps.bar_of(ps.dq)], ps.dpar, p.wait_ns)) {
+        if (!timed_out && !mbar_wait_bounded(&sh.bars[K], par, p.wait_ns)) {
             atomicExch(p.flag, 1);
             timed_out = 1;
         }
         consumed = q + 1;
-        const unsigned char* s0 = sh.shal + ps.sq;
+        const unsigned char* s0 = sh.shal + SQ;
         const float2 u2 = *(const float2*)(s0 + 8 * t);
         if (sg.r_s) {
             const uint32_t rw = *(const uint32_t*)(s0 + 8 * W + 4 * t);
@@ -129,8 +145,10 @@ __device__ __forceinline__ bool c2_iter(const Tb2dParams& p, const Seg& sg, cons
             R[0][NXT][1] = 0.0f;
         }
         if (i >= 1) {
-            const float* s1 = (const float*)(sh.shal + ps.s1);
-            const float* s2 = (const float*)(sh.shal + ps.s2);
+            // rows i-1 (centre) and i-2 (south; row i-1 again at i = 1, where
+            // the south row does not exist and D0 only feeds halo rows)
+            const float* s1 = (const float*)(sh.shal + S1);
+            const float* s2 = (const float*)(sh.shal + (i >= 2 ? S2 : S1));
             const float2 a = *(const float2*)(s1 + kC * t);
             const float2 b = *(const float2*)(s2 + kC * t);
             const float xl = s1[(kC * t + W - 1) % W], xr = s1[(kC * t + kC) % W];
@@ -143,16 +161,16 @@ __device__ __forceinline__ bool c2_iter(const Tb2dParams& p, const Seg& sg, cons
     }
 
     // ---- levels: level l advances row i-1-l -----------------------------------
-    const float* xr = sh.xbuf + (size_t)((i & 1) ^ 1) * S::xbuf_floats;
+    const float* xr = sh.xbuf + (size_t)((K & 1) ^ 1) * S::xbuf_floats;
     const int tl = (t + NT - 1) % NT, tr = (t + 1) % NT;
     const f2_t dt2 = f2_pack(p.dt, p.dt), m4 = f2_pack(-4.0f, -4.0f);
     float dout[kC], vout[kC];
 #pragma unroll
     for (int l = 0; l < B; ++l) {
-        const unsigned char* drow = sh.deep + ps.lev[l];
+        const unsigned char* drow = sh.deep + dslot(-1 - l);
         float vin[kC];
         if (l == 0) {
-            const float2 v2 = *(const float2*)(sh.shal + ps.s1 + 4 * W + 8 * t);
+            const float2 v2 = *(const float2*)(sh.shal + S1 + 4 * W + 8 * t);
             vin[0] = v2.x;
             vin[1] = v2.y;
         } else {
@@ -235,7 +253,7 @@ __device__ __forceinline__ bool c2_iter(const Tb2dParams& p, const Seg& sg, cons
     }
 
     // ---- shared stores, read only after the barrier ------------------------------
-    float* xw = sh.xbuf + (size_t)(i & 1) * S::xbuf_floats;
+    float* xw = sh.xbuf + (size_t)(K & 1) * S::xbuf_floats;
 #pragma unroll
     for (int l = 0; l < B; ++l) {
         if (MID || l < L) {   // level l's next input row: its edges, read by level l next row
@@ -244,8 +262,7 @@ __device__ __forceinline__ bool c2_iter(const Tb2dParams& p, const Seg& sg, cons
         }
     }
     if (have_row && i >= 1)
-        *(float2*)(sh.deep + ps.lev[0] + 16 * t + 8) = make_float2(d0n[0], d0n[1]);
-    ps.advance();
+        *(float2*)(sh.deep + dslot(-1) + 16 * t + 8) = make_float2(d0n[0], d0n[1]);
     // one barrier per row; it also makes the abort decision uniform
     return __syncthreads_or(timed_out) != 0;
 }
@@ -279,7 +296,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) fine_tb2d_c2_kernel(const Tb2dPa
     // per-CTA row ranges of equal cost: rows + (L + B) steps per segment
     const int64_t r_begin = balanced_row(p.rows_total, n, L + B, blockIdx.x, gridDim.x);
     const int64_t r_end = balanced_row(p.rows_total, n, L + B, blockIdx.x + 1, gridDim.x);
-    uint32_t issued = 0, consumed = 0;
+    // ring positions: a segment occupies [base, base + niter) and the next one
+    // starts at the following multiple of kU; positions that receive no copy
+    // get a plain arrival, so slot s completes its phase j at position j kU + s
+    uint32_t pos = 0, consumed = 0, issued_end = 0;
     int timed_out = 0;
     bool aborted = false;
 
@@ -296,20 +316,17 @@ __global__ void __launch_bounds__(NT, 512 / NT) fine_tb2d_c2_kernel(const Tb2dPa
         sg.u_s = p.u_in + slice * pts;
         sg.v_s = p.v_in + slice * pts;
         sg.r_s = p.r_in ? p.r_in + slice * pts : nullptr;
-        sg.base = issued;
+        sg.base = pos;
         int ylo = (ya - L) % n;
         sg.ylo = ylo < 0 ? ylo + n : ylo;
         const int niter = sg.H + L + B;
 
-        C2Pos<NT, B> ps;
-        ps.init(sg.base);
         if (t == 0) {
             for (int rho = 0; rho < kPre && rho < sg.nload; ++rho) {
-                const uint32_t qq = sg.base + (uint32_t)rho;
-                c2_issue<NT, B>(p, sg, sh, rho, (qq % kRD) * S::deep_row, (qq % kRS) * S::sh_row);
+                c2_issue<NT, B>(p, sg, sh, rho, (uint32_t)rho * S::deep_row, (uint32_t)rho * S::sh_row);
+                issued_end = pos + (uint32_t)rho + 1;
             }
         }
-        issued += (uint32_t)sg.nload;
 
         float R[B][3][kC], VV[B][3][kC];
 #pragma unroll
@@ -319,24 +336,32 @@ __global__ void __launch_bounds__(NT, 512 / NT) fine_tb2d_c2_kernel(const Tb2dPa
 #pragma unroll
                 for (int k = 0; k < kC; ++k) R[l][s][k] = VV[l][s][k] = 0.0f;
 
+        uint32_t par = (pos / kU) & 1u;
         int i = 0;
-        for (; i + 3 <= niter; i += 3) {
-            if (c2_iter<NT, B, MID, 0>(p, sg, sh, i, R, VV, ps, timed_out, consumed) ||
-                c2_iter<NT, B, MID, 1>(p, sg, sh, i + 1, R, VV, ps, timed_out, consumed) ||
-                c2_iter<NT, B, MID, 2>(p, sg, sh, i + 2, R, VV, ps, timed_out, consumed)) {
-                aborted = true;
-                break;
-            }
+#define PR_C2_STEP(K)                                                                             \
+    if (i >= niter) break;                                                                         \
+    if (c2_iter<NT, B, MID, K>(p, sg, sh, i, par, R, VV, timed_out, consumed, issued_end)) {       \
+        aborted = true;                                                                            \
+        break;                                                                                     \
+    }                                                                                              \
+    ++i;
+        for (;;) {
+            PR_C2_STEP(0) PR_C2_STEP(1) PR_C2_STEP(2) PR_C2_STEP(3) PR_C2_STEP(4) PR_C2_STEP(5)
+            PR_C2_STEP(6) PR_C2_STEP(7) PR_C2_STEP(8) PR_C2_STEP(9) PR_C2_STEP(10) PR_C2_STEP(11)
+            par ^= 1u;
         }
-        if (!aborted && i < niter)
-            aborted = c2_iter<NT, B, MID, 0>(p, sg, sh, i, R, VV, ps, timed_out, consumed);
-        if (!aborted && i + 1 < niter)
-            aborted = c2_iter<NT, B, MID, 1>(p, sg, sh, i + 1, R, VV, ps, timed_out, consumed);
+#undef PR_C2_STEP
+        if (aborted) break;
+        // close the lap: complete the phases of the positions that got no copy
+        const uint32_t next = (pos + (uint32_t)niter + kU - 1) / kU * kU;
+        if (t == 0)
+            for (uint32_t q = pos + (uint32_t)sg.nload; q < next; ++q) mbar_arrive(&sh.bars[q % kU]);
+        pos = next;
     }
     if (aborted && t == 0) {
         // let copies still in flight land before the CTA's shared memory is released
-        for (uint32_t q = consumed; q < issued; ++q)
-            (void)mbar_wait_bounded(&sh.bars[q % kRD], (q / kRD) & 1u, p.wait_ns / 10);
+        for (uint32_t q = consumed; q < issued_end; ++q)
+            (void)mbar_wait_bounded(&sh.bars[q % kU], (q / kU) & 1u, p.wait_ns / 10);
     }
 }
 

@@ -112,53 +112,6 @@ struct Tb2dParams {
     uint64_t wait_ns;     // limit of each bounded mbarrier wait
 };
 
-// Ring positions of the current row q of a row-streaming fused kernel, as byte
-// offsets into its two shared-memory rings: the deep ring (RD rows of DROW
-// bytes: kappa and D0, read by the B levels at rows q-1 .. q-B, one mbarrier
-// per slot) and the shallow ring (RS rows of SROW bytes: u_hi, u_t, residual,
-// read at rows q, q-1, q-2).  The producer fills row q + PRE.  Positions
-// advance by one row per pipeline step without any division by the ring
-// sizes; the per-level offsets shift down one level per row.
-template <int B, int RD, uint32_t DROW, int RS, uint32_t SROW, int PRE>
-struct RingPos {
-    uint32_t dq;      // deep slot of row q
-    uint32_t dpar;    // phase parity of that slot's mbarrier for row q
-    uint32_t sq;      // shallow slot of row q
-    uint32_t dn, sn;  // slots of row q + PRE (the producer's target)
-    uint32_t lev[B];  // deep slots of rows q-1 .. q-B (level l reads lev[l])
-    uint32_t s1, s2;  // shallow slots of rows q-1, q-2
-
-    __device__ __forceinline__ void init(uint32_t q) {
-        dq = (q % RD) * DROW;
-        dpar = (q / RD) & 1u;
-        sq = (q % RS) * SROW;
-        dn = ((q + PRE) % RD) * DROW;
-        sn = ((q + PRE) % RS) * SROW;
-#pragma unroll
-        for (int l = 0; l < B; ++l) lev[l] = ((q + (uint32_t)(RD * B) - 1u - l) % RD) * DROW;
-        s1 = ((q + 2u * RS - 1u) % RS) * SROW;
-        s2 = ((q + 2u * RS - 2u) % RS) * SROW;
-    }
-    __device__ __forceinline__ void advance() {
-        constexpr uint32_t dbytes = RD * DROW, sbytes = RS * SROW;
-#pragma unroll
-        for (int l = B - 1; l > 0; --l) lev[l] = lev[l - 1];
-        lev[0] = dq;
-        s2 = s1;
-        s1 = sq;
-        dq += DROW;
-        if (dq == dbytes) {
-            dq = 0;
-            dpar ^= 1u;
-        }
-        sq = sq + SROW == sbytes ? 0u : sq + SROW;
-        dn = dn + DROW == dbytes ? 0u : dn + DROW;
-        sn = sn + SROW == sbytes ? 0u : sn + SROW;
-    }
-    // mbarrier index of a deep slot offset
-    __device__ __forceinline__ static uint32_t bar_of(uint32_t doff) { return doff / DROW; }
-};
-
 // First row of CTA b's share when the N*n rows of a batch of N slices are cut
 // into G contiguous ranges of equal cost.  A range is processed slice by
 // slice, and every segment costs its rows plus K pipeline steps of halo and
