@@ -442,6 +442,8 @@ def run_ours(a) -> int:
     c = torch.tensor(w.c, dtype=torch.float32, device=dev)
     ctx = binding.pr_create(w.dim, w.n_fine, w.ratio, c, w.dt_f, w.dt_c, w.n_slices, w.t_final,
                             block_depth=a.block_depth)
+    if a.columns:
+        binding.pr_set_fused_columns(ctx, a.columns)
     info = binding.pr_info(ctx)
     u_in = u_pin.to(dev)
     v_in = v_pin.to(dev)
@@ -545,6 +547,7 @@ def run_ours(a) -> int:
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": dict(workload_desc(w), l2=l2_note, block_depth=info["block_depth"],
+                           columns_per_thread=a.columns or "library default",
                            parallelism=f"replica per GPU x{world}"),
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -568,6 +571,8 @@ def main(argv=None) -> int:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="3")
     ap.add_argument("--block-depth", type=int, default=0, help="0 = library default")
+    ap.add_argument("--columns", type=int, default=0, choices=[0, 2, 4],
+                    help="fused-kernel columns per thread (0 = library default)")
     ap.add_argument("--slices", type=int, default=0,
                     help="propagate only this many slices (smaller profiling runs; 0 = all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -230,7 +230,7 @@ pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void* const* u_i
 pr_status pr_batch_launch(pr_batch* b, void* stream);
 
 /* pr_batch_info -- chosen block depth, fused-kernel columns per thread (0 =
- * chosen by width; see pr_set_fused_columns) and the timed sweep (ms) of
+ * the default; see pr_set_fused_columns) and the timed sweep (ms) of
  * instance i.  Any output pointer may be NULL. */
 pr_status pr_batch_info(const pr_batch* b, int i, int* block_depth, int* columns, double* tuned_ms);
 
@@ -239,9 +239,10 @@ void pr_batch_destroy(pr_batch* b);
 
 /* pr_set_fused_columns -- thread geometry of the fused 2D FP32 passes of
  * this context: 2 or 4 grid columns per thread (n/2 or n/4 threads per row),
- * or 0 = by grid width (2 for n <= 512, 4 for n = 1024, the faster of the two
- * on a GB300).  Both compute the same level recurrence; results agree to
- * rounding.  PR_EINVAL for any other value.  Takes effect at the next call. */
+ * or 0 = the default (4, the faster geometry on a GB300 at n = 512 and 1024;
+ * n = 2048 always runs four columns in x-strips).  Both compute the same level
+ * recurrence; results agree to rounding.  PR_EINVAL for any other value.
+ * Takes effect at the next call. */
 pr_status pr_set_fused_columns(pr_ctx* ctx, int columns);
 
 /* pr_debug_stall_waits -- test hook for the time-out path.  While enabled,

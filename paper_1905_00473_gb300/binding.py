@@ -343,7 +343,7 @@ class Batch:
         _check(load().pr_batch_launch(self.handle, ctypes.c_void_p(_stream_ptr(stream))), None)
 
     def info(self, i):
-        """(block depth, fused columns per thread (0 = by width), tuned ms) of instance i."""
+        """(block depth, fused columns per thread (0 = the default), tuned ms) of instance i."""
         d, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         _check(load().pr_batch_info(self.handle, i, ctypes.byref(d), ctypes.byref(c), ctypes.byref(ms)),
                None)

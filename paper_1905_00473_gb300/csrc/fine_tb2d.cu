@@ -537,13 +537,14 @@ pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     if (ps.levels == 1) return pr_launch_fine_naive(ctx, ps, st);
     if ((ps.r_in || ps.r_out) && ps.rfmt != PR_RESID_BF16)
         return pr_fail(ctx, PR_EINVAL, "tb2d: the fused pass carries a bfloat16 residual");
-    // Thread geometry (pr_set_fused_columns); by default two columns per thread
-    // (fine_tb2d_c2.cu) for n <= 512, where four columns leave too few warps
-    // per SM (n = 512: one CTA of 4 warps), and four (this file) for n = 1024,
-    // where 8 warps fill the SM and the x-neighbour exchange and per-row
-    // overhead are shared by twice the columns.
-    // n = 2048 runs in x-strips with four columns per thread whatever is set.
-    const int cols = ctx->tb_cols ? ctx->tb_cols : (ctx->n <= 512 ? 2 : 4);
+    // Thread geometry (pr_set_fused_columns); by default four columns per
+    // thread (this file) at every width: with static rings it is the faster
+    // geometry on a GB300 at n = 512 and 1024 as well (8 warps per SM, the
+    // x-neighbour exchange and per-row overhead shared by four columns), and
+    // two columns per thread (fine_tb2d_c2.cu, twice the warps) stays
+    // selectable.  n = 2048 runs in x-strips with four columns per thread
+    // whatever is set.
+    const int cols = ctx->tb_cols ? ctx->tb_cols : 4;
     if (cols == 2 && ctx->n <= 1024) return pr_launch_fine_tb2d_c2(ctx, ps, st);
     const int B = ctx->block_depth;
     if (ps.levels < 1 || ps.levels > B) return pr_fail(ctx, PR_EINVAL, "tb2d: bad level count");

@@ -20,7 +20,7 @@ struct pr_ctx {
     double T = 0, dt_com = 0, dt_f = 0, dt_c = 0, dx = 0;
     int m_f = 0, m_c = 0;
     int block_depth = 1;      // fine steps (kicks) per HBM pass
-    int tb_cols = 0;          // fused 2D kernel: columns per thread (0 = by width)
+    int tb_cols = 0;          // fused 2D kernel: columns per thread (0 = default, 4)
     double cmax = 0;
     void* kappa = nullptr;    // dtype, c^2 dt_f / dx^2
     float* kappa_il = nullptr;  // 2D FP32: kappa per thread pair [y][x/2][k0 k1 0 0] (fine_tb2d_c2.cu)

@@ -98,3 +98,40 @@ def test_autograd_gradcheck(lib):
     p0 = torch.tensor(rng.standard_normal(w.shape), device="cuda", requires_grad=True)
     f = lambda c_, a, b: autograd.serial_fine_solve(c_, a, b, w.dt_f, w.m_f, w.n_slices)
     assert torch.autograd.gradcheck(f, (c, u0, p0), eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
+def test_adjoint_full_size_dot_product_3d(lib):
+    """The differentiation workload at full size (256^3, 32 slices of 64 fine
+    steps, FP32), where the FP64 oracle adjoint would take hours: the map
+    (u0, p0) -> (u, u_t)(T) of the serial fine solve is linear, so the input
+    gradients of pr_adjoint for the output gradient y = F x must satisfy
+    <x, F^T y> = <F x, y> = ||F x||^2 (the dot-product identity), here with a
+    smooth random x; the per-slice checkpoint and recompute path runs at the
+    size it exists for."""
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = W.config5()
+    n, N = w.n_fine, w.n_slices
+    c = torch.tensor(w.c, dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(5)
+    x, y_, z = W.node_coords(3, n)
+    fields = []
+    for _ in range(2):
+        f = np.zeros(w.shape)
+        for _ in range(4):
+            k = rng.integers(-6, 7, size=3)
+            f += rng.standard_normal() * np.cos(2 * math.pi * (k[0] * x + k[1] * y_ + k[2] * z) + rng.uniform(0, 6.3))
+        fields.append(torch.tensor(f, dtype=torch.float32, device="cuda"))
+    u0, p0 = fields[0], fields[1] * 4.0
+    ctx1 = binding.pr_create(3, n, 1, c, w.dt_f, w.dt_f, 1, w.dt_com)
+    u, v = u0.clone(), p0.clone()
+    for _ in range(N):
+        binding.pr_fine_all_slices(ctx1, u, v, u, v)
+    ctx = binding.pr_create(3, n, 1, c, w.dt_f, w.dt_f, N, w.t_final)
+    gc, gu0, gp0 = (torch.zeros_like(u0) for _ in range(3))
+    binding.pr_adjoint(ctx, u0, p0, u, v, gc, gu0, gp0)
+    torch.cuda.synchronize()
+    lhs = float(torch.sum(u.double() ** 2) + torch.sum(v.double() ** 2))
+    rhs = float(torch.sum(u0.double() * gu0.double()) + torch.sum(p0.double() * gp0.double()))
+    assert math.isfinite(lhs) and lhs > 0
+    assert abs(lhs - rhs) <= 1e-4 * lhs, (lhs, rhs)
