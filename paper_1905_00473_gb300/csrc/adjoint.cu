@@ -16,32 +16,27 @@
 // Arithmetic is plain in the context dtype; dL/dkappa accumulates in FP64.
 #include <stdio.h>
 
+#include "grid_rows.cuh"
 #include "pr_internal.cuh"
 
 namespace {
 
 constexpr int kT = 256;
 
-template <int DIM>
-__device__ __forceinline__ void nbrs(int64_t p, int64_t n, int64_t* nb) {
-    int64_t stride = 1, rem = p;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-        const int64_t i = rem % n;
-        rem /= n;
-        nb[2 * a] = p + (((i + 1 == n) ? 0 : i + 1) - i) * stride;
-        nb[2 * a + 1] = p + (((i == 0) ? n - 1 : i - 1) - i) * stride;
-        stride *= n;
-    }
-}
+// The level kernels index one slice row-wise (grid_rows.cuh): x from the
+// thread, the (z, y) row from a grid-stride loop over blockIdx.y.
 
 // forward level with trace: v += w kappa D(u_g) in place; u_{g+1} -> un
 template <typename T, int DIM>
 __global__ void fwd_level(const T* __restrict__ u, T* __restrict__ v, T* __restrict__ un,
                           const T* __restrict__ kap, int64_t n, int64_t pts, T w, T dt, int drift) {
-    for (int64_t p = (int64_t)blockIdx.x * kT + threadIdx.x; p < pts; p += (int64_t)gridDim.x * kT) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    for (int64_t row = blockIdx.y; row < pts / n; row += gridDim.y) {
+        const rows::Row rw = rows::row_of<DIM>(row, n, pts);
+        const int64_t p = rw.off + x;
         int64_t nb[2 * DIM];
-        nbrs<DIM>(p, n, nb);
+        rows::nbrs_of<DIM>(rw, x, n, nb);
         const T u0 = u[p];
         T lap = 0;
 #pragma unroll
@@ -56,9 +51,13 @@ template <typename T, int DIM>
 __global__ void adj_level(const T* __restrict__ lu, const T* __restrict__ lv, const T* __restrict__ ug,
                           const T* __restrict__ kap, T* __restrict__ lu_o, T* __restrict__ lv_o,
                           double* __restrict__ gk, int64_t n, int64_t pts, T w, T dt, int drift) {
-    for (int64_t p = (int64_t)blockIdx.x * kT + threadIdx.x; p < pts; p += (int64_t)gridDim.x * kT) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    for (int64_t row = blockIdx.y; row < pts / n; row += gridDim.y) {
+        const rows::Row rw = rows::row_of<DIM>(row, n, pts);
+        const int64_t p = rw.off + x;
         int64_t nb[2 * DIM];
-        nbrs<DIM>(p, n, nb);
+        rows::nbrs_of<DIM>(rw, x, n, nb);
         const T mu = drift ? lv[p] + dt * lu[p] : lv[p];
         const T kmu = kap[p] * mu;
         T dkm = 0, du = 0;
@@ -73,6 +72,82 @@ __global__ void adj_level(const T* __restrict__ lu, const T* __restrict__ lv, co
         gk[p] += (double)w * (double)du * (double)mu;
         lu_o[p] = lu[p] + w * dkm;
         lv_o[p] = mu;
+    }
+}
+
+// FP32 forms of the two level kernels with four consecutive points per thread
+// (n % 4 == 0): 128-bit quads of every field and of its y/z neighbours
+// (grid_rows.cuh), the same arithmetic in the same order per point.
+template <int DIM>
+__global__ void fwd_level_x4(const float* __restrict__ u, float* __restrict__ v, float* __restrict__ un,
+                             const float* __restrict__ kap, int64_t n, int64_t pts, float w, float dt, int drift) {
+    typedef rows::Quad<DIM, float, float4> Q;
+    const int64_t x0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= n) return;
+    int64_t xl, xr;
+    rows::quad_edges(x0, n, &xl, &xr);
+    for (int64_t row = blockIdx.y; row < pts / n; row += gridDim.y) {
+        const rows::Row rw = rows::row_of<DIM>(row, n, pts);
+        const int64_t p = rw.off + x0;
+        const Q uq = rows::load_quad<DIM, float, float4>(u, rw, x0, xl, xr);
+        const float4 k4 = *(const float4*)(kap + p);
+        const float4 v4 = *(const float4*)(v + p);
+        float vn[4], u1[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float u0 = Q::comp(uq.c, j);
+            float lap = 0;
+#pragma unroll
+            for (int k = 0; k < 2 * DIM; ++k) lap += (uq.nb(j, k) - u0);
+            vn[j] = Q::comp(v4, j) + w * Q::comp(k4, j) * lap;
+            u1[j] = u0 + dt * vn[j];
+        }
+        *(float4*)(v + p) = make_float4(vn[0], vn[1], vn[2], vn[3]);
+        if (drift) *(float4*)(un + p) = make_float4(u1[0], u1[1], u1[2], u1[3]);
+    }
+}
+
+template <int DIM>
+__global__ void adj_level_x4(const float* __restrict__ lu, const float* __restrict__ lv,
+                             const float* __restrict__ ug, const float* __restrict__ kap,
+                             float* __restrict__ lu_o, float* __restrict__ lv_o, double* __restrict__ gk,
+                             int64_t n, int64_t pts, float w, float dt, int drift) {
+    typedef rows::Quad<DIM, float, float4> Q;
+    const int64_t x0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= n) return;
+    int64_t xl, xr;
+    rows::quad_edges(x0, n, &xl, &xr);
+    for (int64_t row = blockIdx.y; row < pts / n; row += gridDim.y) {
+        const rows::Row rw = rows::row_of<DIM>(row, n, pts);
+        const int64_t p = rw.off + x0;
+        const Q lvq = rows::load_quad<DIM, float, float4>(lv, rw, x0, xl, xr);
+        const Q luq = rows::load_quad<DIM, float, float4>(lu, rw, x0, xl, xr);
+        const Q kq = rows::load_quad<DIM, float, float4>(kap, rw, x0, xl, xr);
+        const Q gq = rows::load_quad<DIM, float, float4>(ug, rw, x0, xl, xr);
+        const double2 g01 = *(const double2*)(gk + p), g23 = *(const double2*)(gk + p + 2);
+        double go[4] = {g01.x, g01.y, g23.x, g23.y};
+        float luo[4], lvo[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float lvj = Q::comp(lvq.c, j), luj = Q::comp(luq.c, j);
+            const float mu = drift ? lvj + dt * luj : lvj;
+            const float kmu = Q::comp(kq.c, j) * mu;
+            float dkm = 0, du = 0;
+            const float u0 = Q::comp(gq.c, j);
+#pragma unroll
+            for (int k = 0; k < 2 * DIM; ++k) {
+                const float muq = drift ? lvq.nb(j, k) + dt * luq.nb(j, k) : lvq.nb(j, k);
+                dkm += kq.nb(j, k) * muq - kmu;
+                du += gq.nb(j, k) - u0;
+            }
+            go[j] += (double)w * (double)du * (double)mu;
+            luo[j] = luj + w * dkm;
+            lvo[j] = mu;
+        }
+        *(double2*)(gk + p) = make_double2(go[0], go[1]);
+        *(double2*)(gk + p + 2) = make_double2(go[2], go[3]);
+        *(float4*)(lu_o + p) = make_float4(luo[0], luo[1], luo[2], luo[3]);
+        *(float4*)(lv_o + p) = make_float4(lvo[0], lvo[1], lvo[2], lvo[3]);
     }
 }
 
@@ -116,13 +191,38 @@ pr_status run(pr_ctx* ctx, const T* u0, const T* p0, const T* guT, const T* gvT,
     const T dt = (T)ctx->dt_f;
     auto w_of = [&](int g) { return (T)((g == 0 || g == m) ? 0.5 : 1.0); };
     const int nb = nblocks(pts);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    // level kernels: one slice, row-wise; FP32 grids with n % 4 == 0 take
+    // four points per thread
+    const bool quads = sizeof(T) == 4 && n % 4 == 0;
+    dim3 lvl_grid, lvl_block;
+    rows::shape_for(quads ? n / 4 : n, pts / n, sms > 0 ? sms : 1, &lvl_grid, &lvl_block);
+    auto fwd = [&](const T* u, T* v, T* un, int g) {
+        if constexpr (sizeof(T) == 4) {
+            if (quads) {
+                fwd_level_x4<DIM><<<lvl_grid, lvl_block, 0, st>>>(u, v, un, kap, n, pts, w_of(g), dt, g < m);
+                return;
+            }
+        }
+        fwd_level<T, DIM><<<lvl_grid, lvl_block, 0, st>>>(u, v, un, kap, n, pts, w_of(g), dt, g < m);
+    };
+    auto adj = [&](const T* lu, const T* lv, const T* ug, T* lu_o, T* lv_o, int g) {
+        if constexpr (sizeof(T) == 4) {
+            if (quads) {
+                adj_level_x4<DIM><<<lvl_grid, lvl_block, 0, st>>>(lu, lv, ug, kap, lu_o, lv_o, gk, n, pts, w_of(g),
+                                                                 dt, g < m);
+                return;
+            }
+        }
+        adj_level<T, DIM><<<lvl_grid, lvl_block, 0, st>>>(lu, lv, ug, kap, lu_o, lv_o, gk, n, pts, w_of(g), dt, g < m);
+    };
 
     auto recompute = [&](int s) {   // trace of slice s from its checkpoint; leaves v in vw
         cudaMemcpyAsync(tr, cu + (size_t)s * pts, fb, cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(vw, cv + (size_t)s * pts, fb, cudaMemcpyDeviceToDevice, st);
         for (int g = 0; g <= m; ++g)
-            fwd_level<T, DIM><<<nb, kT, 0, st>>>(tr + (size_t)g * pts, vw, tr + (size_t)(g + 1 <= m ? g + 1 : g) * pts,
-                                                 kap, n, pts, w_of(g), dt, g < m);
+            fwd(tr + (size_t)g * pts, vw, tr + (size_t)(g + 1 <= m ? g + 1 : g) * pts, g);
     };
     // forward: checkpoints
     cudaMemcpyAsync(cu, u0, fb, cudaMemcpyDeviceToDevice, st);
@@ -140,8 +240,7 @@ pr_status run(pr_ctx* ctx, const T* u0, const T* p0, const T* guT, const T* gvT,
     for (int s = N - 1; s >= 0; --s) {
         recompute(s);
         for (int g = m; g >= 0; --g) {
-            adj_level<T, DIM><<<nb, kT, 0, st>>>(la[cur], lb[cur], tr + (size_t)g * pts, kap, la[cur ^ 1],
-                                                 lb[cur ^ 1], gk, n, pts, w_of(g), dt, g < m);
+            adj(la[cur], lb[cur], tr + (size_t)g * pts, la[cur ^ 1], lb[cur ^ 1], g);
             cur ^= 1;
         }
     }

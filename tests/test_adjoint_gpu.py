@@ -35,7 +35,8 @@ def _gpu_adjoint(w, dtype, N, u0, p0, gu, gv):
 
 
 @pytest.mark.parametrize("dim,n,N,m,dtype", [(2, 24, 3, 8, "f64"), (3, 12, 2, 6, "f64"),
-                                             (1, 48, 4, 10, "f64"), (2, 64, 3, 12, "f32")])
+                                             (1, 48, 4, 10, "f64"), (2, 64, 3, 12, "f32"),
+                                             (3, 16, 2, 6, "f32"), (2, 18, 3, 8, "f32")])
 def test_adjoint_matches_oracle(lib, dim, n, N, m, dtype):
     w = W.custom_case(dim, n, N, m, dtype)
     rng = np.random.default_rng(dim)

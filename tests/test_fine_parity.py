@@ -97,6 +97,17 @@ def test_single_level_path_matches_oracle(lib, dim, n, m_f, N, dtype):
     _check_all(w, ctx, u, v)
 
 
+@pytest.mark.parametrize("dim,n,m_f,N", [(2, 18, 9, 3), (1, 30, 11, 2), (3, 10, 5, 2)])
+def test_single_level_path_width_not_multiple_of_4(lib, dim, n, m_f, N):
+    """Widths the four-point form of the one-level kernel does not take fall
+    back to one point per thread (coarse ratio 2 keeps n/ratio integral)."""
+    w = W.custom_case(dim, n, N, m_f, "f32")
+    w.ratio = 2
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=6)
+    _check_all(w, ctx, u, v)
+
+
 def test_forced_single_level_path_on_fused_geometry(lib):
     w = W.custom_case(2, 256, 2, 10, "f32", "inclusion")
     ctx = P.make_ctx(w, block_depth=1)
