@@ -43,11 +43,12 @@
 // L-row halo above and below (periodic in y), and the cut points balance
 // rows plus the halo and drain steps of every segment (balanced_row).
 //
-// Variants.  MID = a pass strictly inside the sweep (no half kick, every
-// level drifts, all B levels active), which is nearly every pass; the
-// general variant handles the first pass (half kick at g = 0), the last pass
-// (half kick at g = m, no drift, fewer than B levels: the missing levels pass
-// rows through unchanged).
+// Variants.  MID = a pass in which all B levels kick and drift and a residual
+// goes out: the middle passes (no half kick) and, with HALF0, the first pass
+// (half kick at level 0, no residual in).  The general variant handles the
+// last pass (half kick at g = m, no drift, fewer than B levels: the missing
+// levels pass rows through unchanged).  At depth 8 the last pass may hold 9
+// levels, so that a sweep of 8 k + 1 levels needs no one-level pass.
 #include "pr_internal.cuh"
 #include "tb_common.cuh"
 
@@ -145,7 +146,7 @@ __device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, un
 //   VV[l][.] u_t of level l's input row: read (K+2)%3, written K%3
 // `par` is the mbarrier phase parity of the current ring lap.  Returns true
 // when some thread's bounded wait gave up.
-template <int NT, int B, int XH, bool MID, int K>
+template <int NT, int B, int XH, bool MID, bool HALF0, int K>
 __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, unsigned char* sm, int i,
                                           uint32_t par, uint32_t h6, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
                                           int& timed_out, uint32_t& consumed, uint32_t& issued_end,
@@ -209,12 +210,27 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
             const float c[4] = {a.x, a.y, a.z, a.w};
             const float s2v[4] = {b2.x, b2.y, b2.z, b2.w};
             const float xl = s1[(kCpt * t + W - 1) % W], xrr = s1[(kCpt * t + kCpt) % W];
+#if PR_TB2D_PACKED
+            // columns (0,1) and (2,3) as f32x2 pairs, the same operations per lane
+            const f2_t cp[2] = {f2_pack(c[0], c[1]), f2_pack(c[2], c[3])};
+            const f2_t lp[2] = {f2_pack(xl, c[0]), f2_pack(c[1], c[2])};
+            const f2_t rp[2] = {f2_pack(c[1], c[2]), f2_pack(c[3], xrr)};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const f2_t sp = f2_pack(s2v[2 * h], s2v[2 * h + 1]), up = f2_pack(uu[2 * h], uu[2 * h + 1]);
+                const f2_t d = f2_add(f2_add(f2_sub(lp[h], cp[h]), f2_sub(rp[h], cp[h])),
+                                      f2_add(f2_sub(sp, cp[h]), f2_sub(up, cp[h])));
+                d0n[2 * h] = f2_lo(d);
+                d0n[2 * h + 1] = f2_hi(d);
+            }
+#else
 #pragma unroll
             for (int k = 0; k < kCpt; ++k) {
                 const float left = k == 0 ? xl : c[k - 1];
                 const float right = k == kCpt - 1 ? xrr : c[k + 1];
                 d0n[k] = ((left - c[k]) + (right - c[k])) + ((s2v[k] - c[k]) + (uu[k] - c[k]));
             }
+#endif
         }
     } else {
 #pragma unroll
@@ -252,6 +268,10 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
             const float xl = xr[l * 2 * NT + NT + tl];
             const float xrt = xr[l * 2 * NT + tr];
             bool dr = true;
+            if (MID && HALF0 && l == 0) {   // the first pass: level 0 is g = 0
+#pragma unroll
+                for (int k = 0; k < kCpt; ++k) kk[k] *= 0.5f;
+            }
             if (!MID) {
                 const int g = p.g0 + l;
                 if (g == 0 || g == p.m) {
@@ -324,8 +344,21 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
         float uo[4];
         if (MID || p.r_out) {
             float rr[4];
+#if PR_TB2D_PACKED
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                f2_t r2;
+                const f2_t s2 = f2_two_sum(f2_pack(u0[2 * h], u0[2 * h + 1]),
+                                           f2_pack(dout[2 * h], dout[2 * h + 1]), &r2);
+                uo[2 * h] = f2_lo(s2);
+                uo[2 * h + 1] = f2_hi(s2);
+                rr[2 * h] = f2_lo(r2);
+                rr[2 * h + 1] = f2_hi(r2);
+            }
+#else
 #pragma unroll
             for (int k = 0; k < kCpt; ++k) uo[k] = pr_two_sum(u0[k], dout[k], &rr[k]);
+#endif
             *(uint2*)(p.r_out + off_out) = make_uint2(pr_bf16x2(rr[0], rr[1]), pr_bf16x2(rr[2], rr[3]));
         } else {
 #pragma unroll
@@ -356,7 +389,7 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
 // x-strips of 4 NT columns, of which the middle 4 NT - 2 XH are final (the
 // stencil's reach grows one column per level, so XH >= B), and the rows of a
 // slice are covered by n / (4 NT - 2 XH) strips.
-template <int NT, int B, int XH, bool MID>
+template <int NT, int B, int XH, bool MID, bool HALF0>
 __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     using S = Smem<NT, B>;
     extern __shared__ __align__(128) unsigned char sm[];
@@ -431,7 +464,8 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         int i = 0;
 #define PR_TB2D_STEP(K)                                                                                   \
     if (i >= niter) break;                                                                                 \
-    if (tb2d_step<NT, B, XH, MID, K>(p, sg, sm, i, par, h6, R, VV, timed_out, consumed, issued_end, pol)) { \
+    if (tb2d_step<NT, B, XH, MID, HALF0, K>(p, sg, sm, i, par, h6, R, VV, timed_out, consumed, issued_end,  \
+                                           pol)) {                                                         \
         aborted = true;                                                                                    \
         break;                                                                                             \
     }                                                                                                      \
@@ -460,10 +494,10 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     }
 }
 
-template <int NT, int B, int XH, bool MID>
+template <int NT, int B, int XH, bool MID, bool HALF0>
 pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     using S = Smem<NT, B>;
-    auto kern = fine_tb2d_kernel<NT, B, XH, MID>;
+    auto kern = fine_tb2d_kernel<NT, B, XH, MID, HALF0>;
     static int configured_dev = -1;
     static int blocks_per_sm = 0;
     static int sms = 0;
@@ -502,14 +536,30 @@ pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     return PR_OK;
 }
 
+// Passes in which all B levels kick and drift and a residual goes out run the
+// specialised kernel: the middle passes, and the first pass, which differs
+// only by the half kick at level 0 and no residual in.  The general variant
+// takes the rest (the last pass; passes of fewer levels).
 template <int NT, int B, int XH>
 pr_status launch_depth(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
-    const bool mid = ps.levels == B && ps.g0 >= 1 && ps.g0 + B - 1 < ps.m && ps.r_in && ps.r_out;
-    return mid ? launch_cfg<NT, B, XH, true>(ctx, ps, st) : launch_cfg<NT, B, XH, false>(ctx, ps, st);
+    const bool full = ps.levels == B && ps.g0 + B - 1 < ps.m && ps.r_out;
+    if (full && ps.g0 >= 1 && ps.r_in) return launch_cfg<NT, B, XH, true, false>(ctx, ps, st);
+    if (full && ps.g0 == 0 && !ps.r_in) return launch_cfg<NT, B, XH, true, true>(ctx, ps, st);
+    return launch_cfg<NT, B, XH, false, false>(ctx, ps, st);
 }
 
 template <int B>
 pr_status launch_n(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
+    // depth 8 + 1: the sweep's last pass absorbs the final half-kick level
+    // (general variant only; the 12-row kappa/D0 ring holds 9 + kPre + 1 rows)
+    if (B == 8 && ps.levels == 9) {
+        switch (ctx->n) {
+            case 256: return launch_cfg<64, 9, 0, false, false>(ctx, ps, st);
+            case 512: return launch_cfg<128, 9, 0, false, false>(ctx, ps, st);
+            case 1024: return launch_cfg<256, 9, 0, false, false>(ctx, ps, st);
+            default: return pr_fail(ctx, PR_EINVAL, "tb2d: no depth-9 pass at this width");
+        }
+    }
     switch (ctx->n) {
         case 256: return launch_depth<64, B, 0>(ctx, ps, st);
         case 512: return launch_depth<128, B, 0>(ctx, ps, st);
@@ -533,6 +583,14 @@ bool pr_tb2d_supported(const pr_ctx* ctx, int depth) {
     return ctx->n == 256 || ctx->n == 512 || ctx->n == 1024 || (ctx->n == 2048 && depth == 4);
 }
 
+// whether a pass of block_depth + 1 levels can run fused (four columns per
+// thread, whole rows, depth 8): the sweep's final single level then joins the
+// last pass instead of taking a one-level pass of its own
+bool pr_tb2d_extra_level(const pr_ctx* ctx) {
+    const int cols = ctx->tb_cols ? ctx->tb_cols : 4;
+    return cols == 4 && ctx->block_depth == 8 && pr_tb2d_supported(ctx, 8) && ctx->n <= 1024;
+}
+
 pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     if (ps.levels == 1) return pr_launch_fine_naive(ctx, ps, st);
     if ((ps.r_in || ps.r_out) && ps.rfmt != PR_RESID_BF16)
@@ -547,7 +605,8 @@ pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     const int cols = ctx->tb_cols ? ctx->tb_cols : 4;
     if (cols == 2 && ctx->n <= 1024) return pr_launch_fine_tb2d_c2(ctx, ps, st);
     const int B = ctx->block_depth;
-    if (ps.levels < 1 || ps.levels > B) return pr_fail(ctx, PR_EINVAL, "tb2d: bad level count");
+    if (ps.levels < 1 || ps.levels > B + (pr_tb2d_extra_level(ctx) ? 1 : 0))
+        return pr_fail(ctx, PR_EINVAL, "tb2d: bad level count");
     if (B == 8) return launch_n<8>(ctx, ps, st);
     if (B == 4) return launch_n<4>(ctx, ps, st);
     return pr_fail(ctx, PR_EINVAL, "tb2d: unsupported depth");

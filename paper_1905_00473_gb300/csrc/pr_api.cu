@@ -347,7 +347,12 @@ extern "C" pr_status pr_fine_all_slices(pr_ctx* ctx, const void* u_in, const voi
 
     const int m = ctx->m_f;
     const int levels_total = m + 1;            // m full steps = m + 1 kicks
-    const int passes = (levels_total + depth - 1) / depth;
+    int passes = (levels_total + depth - 1) / depth;
+    // a lone final level joins the previous pass where the fused kernel
+    // takes depth + 1 levels
+    const bool merge_last = depth > 1 && passes >= 2 && levels_total % depth == 1 &&
+                            ctx->dtype == PR_F32 && pr_tb2d_extra_level(ctx);
+    if (merge_last) --passes;
     auto scr_u = [&](int h) { return (char*)ctx->su[h] + off; };
     auto scr_v = [&](int h) { return (char*)ctx->sv[h] + off; };
     auto scr_r = [&](int h) -> void* {
@@ -358,7 +363,7 @@ extern "C" pr_status pr_fine_all_slices(pr_ctx* ctx, const void* u_in, const voi
         pr_pass ps;
         ps.nslices = ns;
         ps.g0 = p * depth;
-        ps.levels = std::min(depth, levels_total - ps.g0);
+        ps.levels = (merge_last && p == passes - 1) ? depth + 1 : std::min(depth, levels_total - ps.g0);
         ps.m = m;
         ps.rfmt = rfmt;
         const bool first = (p == 0), last = (p == passes - 1);

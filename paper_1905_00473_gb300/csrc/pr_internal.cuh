@@ -151,6 +151,8 @@ pr_status pr_launch_fine_naive(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
 // geometry is not supported (caller falls back to the naive path)
 bool pr_tb2d_supported(const pr_ctx* ctx, int depth);
 pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
+// whether the fused kernel takes a pass of block_depth + 1 levels (the last)
+bool pr_tb2d_extra_level(const pr_ctx* ctx);
 // the same passes with two columns per thread (16 warps per SM at n = 1024)
 pr_status pr_launch_fine_tb2d_c2(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
 pr_status pr_launch_energy(pr_ctx* ctx, const void* u, const void* v, int nslices,

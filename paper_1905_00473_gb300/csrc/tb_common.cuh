@@ -89,6 +89,19 @@ __device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// s = a + b and its exact rounding error r = (a + b) - s per lane (TwoSum,
+// Knuth), the same operations as pr_two_sum
+__device__ __forceinline__ f2_t f2_two_sum(f2_t a, f2_t b, f2_t* r) {
+    const f2_t s = f2_add(a, b);
+    const f2_t bb = f2_sub(s, a);
+    *r = f2_add(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb));
+    return s;
+}
 __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
     f2_t r;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));

@@ -97,6 +97,23 @@ def test_single_level_path_matches_oracle(lib, dim, n, m_f, N, dtype):
     _check_all(w, ctx, u, v)
 
 
+@pytest.mark.parametrize("n,m_f", [(256, 8), (256, 16), (512, 24), (1024, 8)])
+def test_first_pass_and_nine_level_last_pass(lib, n, m_f):
+    """Sweeps of 8 k + 1 levels: the first pass runs the specialised kernel
+    with the half kick at level 0, and the lone final level joins the last
+    pass (9 levels), so 9, 17 and 25 levels take 1, 2 and 3 fused passes."""
+    from paper_1905_00473_gb300 import binding
+    w = W.custom_case(2, n, 3, m_f, "f32", "inclusion", seed=n + m_f)
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=8)
+    binding.pr_profile(ctx, True)
+    _check_all(w, ctx, u, v)
+    binding.pr_profile(ctx, False)
+    fused, _ = binding.pr_profile_read(ctx, 0)
+    single, _ = binding.pr_profile_read(ctx, 1)
+    assert (fused, single) == ((m_f + 1) // 8, 0), (fused, single)
+
+
 @pytest.mark.parametrize("dim,n,m_f,N", [(2, 18, 9, 3), (1, 30, 11, 2), (3, 10, 5, 2)])
 def test_single_level_path_width_not_multiple_of_4(lib, dim, n, m_f, N):
     """Widths the four-point form of the one-level kernel does not take fall
