@@ -7,7 +7,7 @@ import numpy as np
 from oracle import energy, fine
 from paper_1905_00473_gb300 import workloads
 
-# Spec tolerance: relative energy-norm error per fine slice in FP32.
+# Required accuracy: relative energy-norm error per fine slice in FP32.
 TOL_ENERGY_F32 = 1e-5
 # FP64: ~m_F roundings of O(1) values, amplified by (dx k)^-1 <= n in the
 # energy norm: 1e-11 leaves two orders of margin for n <= 1024, m_F <= 400.

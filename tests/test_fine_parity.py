@@ -1,8 +1,8 @@
 """GPU parity of pr_fine_all_slices (F over all slices, Alg. 3 parFor; Sec. 3.1
 scheme) against the FP64 oracle on the same seeded inputs.
 
-Bar: relative energy-norm error per slice <= 1e-5 in FP32 (north-star
-tolerance) and <= 1e-11 in FP64; the relative l2 error of u is checked too.
+Bar: relative energy-norm error per slice <= 1e-5 in FP32 (the accuracy
+required of an FP32 fine slice) and <= 1e-11 in FP64; the relative l2 error of u is checked too.
 Small cases span several passes of the fused kernel, a ragged last pass and
 the slice-crossing row ranges of its persistent work split; the full-size
 configurations are checked on sampled slices against the oracle and on every

@@ -3,8 +3,8 @@ oracle: the coarse sweep C R, the initial guess I C R, K iterations with each
 corrector, UpdateSVD (Alg. 1) and finite termination after N iterations.
 
 FP64 contexts are compared to ~1e-9 (same arithmetic, different rounding
-order and FFT library); FP32 contexts against the benchmark spec's bound of 1e-4
-relative energy-norm error for the parareal solution."""
+order and FFT library); FP32 contexts against the bound of 1e-4 relative
+energy-norm error required of the FP32 parareal solution."""
 import json
 import math
 import os
@@ -119,7 +119,7 @@ def test_finite_termination_on_gpu(lib, corrector):
             assert e <= tol, (dtype, corrector, nn, e)
 
 
-def test_fp32_iterations_within_north_star_bound(lib):
+def test_fp32_iterations_within_1e4_energy_bound(lib):
     """FP32 context vs FP64 oracle after K iterations of the Procrustes method:
     relative energy-norm error of every state <= 1e-4."""
     w = _case(2, 256, 6, 16, "f32", 4, "inclusion")
