@@ -61,7 +61,7 @@ typedef struct pr_grid {
 
 /* Options.  block_depth: fine steps fused per HBM pass of the 2D FP32 kernel
  * (0 = library default: 8, or 4 where the width has no depth-8 kernel;
- * 8 or 4 use the fused kernel where it applies: n = 256, 512, 1024, and
+ * 8 or 4 use the fused kernel where it applies: n = 128, 256, 512, 1024, and
  * 2048 at depth 4 only; 1 = one step per pass).  Other fields are reserved
  * for the coarse/correction stages and are ignored by the fine path. */
 typedef struct pr_options {

@@ -554,6 +554,7 @@ pr_status launch_n(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     // (general variant only; the 12-row kappa/D0 ring holds 9 + kPre + 1 rows)
     if (B == 8 && ps.levels == 9) {
         switch (ctx->n) {
+            case 128: return launch_cfg<32, 9, 0, false, false>(ctx, ps, st);
             case 256: return launch_cfg<64, 9, 0, false, false>(ctx, ps, st);
             case 512: return launch_cfg<128, 9, 0, false, false>(ctx, ps, st);
             case 1024: return launch_cfg<256, 9, 0, false, false>(ctx, ps, st);
@@ -561,6 +562,7 @@ pr_status launch_n(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
         }
     }
     switch (ctx->n) {
+        case 128: return launch_depth<32, B, 0>(ctx, ps, st);   // one warp per CTA
         case 256: return launch_depth<64, B, 0>(ctx, ps, st);
         case 512: return launch_depth<128, B, 0>(ctx, ps, st);
         case 1024: return launch_depth<256, B, 0>(ctx, ps, st);
@@ -580,7 +582,7 @@ pr_status launch_n(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
 // shared-memory footprint; the batch autotuner chooses between them)
 bool pr_tb2d_supported(const pr_ctx* ctx, int depth) {
     if (ctx->dim != 2 || ctx->dtype != PR_F32 || (depth != 8 && depth != 4)) return false;
-    return ctx->n == 256 || ctx->n == 512 || ctx->n == 1024 || (ctx->n == 2048 && depth == 4);
+    return ctx->n == 128 || ctx->n == 256 || ctx->n == 512 || ctx->n == 1024 || (ctx->n == 2048 && depth == 4);
 }
 
 // whether a pass of block_depth + 1 levels can run fused (four columns per

@@ -415,6 +415,7 @@ pr_status c2_launch_depth(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
 template <int B>
 pr_status c2_launch_n(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     switch (ctx->n) {
+        case 128: return c2_launch_depth<64, B>(ctx, ps, st);
         case 256: return c2_launch_depth<128, B>(ctx, ps, st);
         case 512: return c2_launch_depth<256, B>(ctx, ps, st);
         case 1024: return c2_launch_depth<512, B>(ctx, ps, st);

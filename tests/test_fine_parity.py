@@ -38,7 +38,9 @@ def _check_all(w, ctx, u, v, slices=None):
     (256, 20, 3, "inclusion"),   # passes of 8, 8, 5 levels; rows split across 3 slices
     (256, 7, 2, "smooth"),       # one full pass of 8 levels
     (256, 1, 2, "smooth"),       # two levels: single short pass
-    (512, 16, 2, "smooth"),      # 17 levels: 8, 8, then a one-level pass
+    (512, 16, 2, "smooth"),      # 17 levels: 8 + 9 (four columns) or 8, 8, 1 (two)
+    (128, 20, 3, "smooth"),      # narrowest tile: one warp per CTA with four columns
+    (128, 15, 1, "inclusion"),   # 16 levels, every CTA's rows inside one slice
     (1024, 12, 1, "inclusion"),  # widest tile, 13 levels
 ])
 def test_fused_2d_matches_oracle(lib, n, m_f, N, medium, cols):
