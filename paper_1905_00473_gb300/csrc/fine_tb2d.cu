@@ -149,6 +149,7 @@ __device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, un
 template <int NT, int B, int XH, bool MID, bool HALF0, int K>
 __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, unsigned char* sm, int i,
                                           uint32_t par, uint32_t h6, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
+                                          float (&UH)[3][kCpt],
                                           int& timed_out, uint32_t& consumed, uint32_t& issued_end,
                                           const Pols& pol) {
     using S = Smem<NT, B>;
@@ -190,6 +191,10 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
         const unsigned char* s0 = S::shal(sm, SQ);
         const float4 u4 = *(const float4*)(s0 + 16 * t);
         const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
+        // u_hi of rows i, i-1, i-2 in a register ring of period 3 (slot K % 3
+        // holds row i), so D0 needs no shared loads for the thread's own columns
+#pragma unroll
+        for (int k = 0; k < kCpt; ++k) UH[CUR][k] = uu[k];
         if (sg.r_s) {
             const uint2 r2 = *(const uint2*)(s0 + W * 8 + 2 * kCpt * t);
             R[0][NXT][0] = pr_bf16_lo(r2.x);
@@ -201,14 +206,12 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
             for (int k = 0; k < kCpt; ++k) R[0][NXT][k] = 0.0f;
         }
         if (i >= 1) {
-            // rows i-1 (centre) and i-2 (south; row i-1 again at i = 1, where
-            // the south row does not exist and D0 only feeds halo rows)
+            // rows i-1 (centre) and i-2 (south) from the register ring; at
+            // i = 1 the south slot holds a stale row, and D0 of row 0 only
+            // feeds halo rows
             const float* s1 = (const float*)S::shal(sm, S1);
-            const float* s2 = (const float*)S::shal(sm, i >= 2 ? S2 : S1);
-            const float4 a = *(const float4*)(s1 + kCpt * t);
-            const float4 b2 = *(const float4*)(s2 + kCpt * t);
-            const float c[4] = {a.x, a.y, a.z, a.w};
-            const float s2v[4] = {b2.x, b2.y, b2.z, b2.w};
+            const float c[4] = {UH[PRV][0], UH[PRV][1], UH[PRV][2], UH[PRV][3]};
+            const float s2v[4] = {UH[NXT][0], UH[NXT][1], UH[NXT][2], UH[NXT][3]};
             const float xl = s1[(kCpt * t + W - 1) % W], xrr = s1[(kCpt * t + kCpt) % W];
 #if PR_TB2D_PACKED
             // columns (0,1) and (2,3) as f32x2 pairs, the same operations per lane
@@ -452,19 +455,23 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
             }
         }
 
-        float R[B][3][kCpt], VV[B][3][kCpt];
+        float R[B][3][kCpt], VV[B][3][kCpt], UH[3][kCpt];
 #pragma unroll
         for (int l = 0; l < B; ++l)
 #pragma unroll
             for (int s = 0; s < 3; ++s)
 #pragma unroll
                 for (int k = 0; k < kCpt; ++k) R[l][s][k] = VV[l][s][k] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) UH[s][k] = 0.0f;
 
         uint32_t lap6 = pos / 6;   // half-laps of the deep ring before this position
         int i = 0;
 #define PR_TB2D_STEP(K)                                                                                   \
     if (i >= niter) break;                                                                                 \
-    if (tb2d_step<NT, B, XH, MID, HALF0, K>(p, sg, sm, i, par, h6, R, VV, timed_out, consumed, issued_end,  \
+    if (tb2d_step<NT, B, XH, MID, HALF0, K>(p, sg, sm, i, par, h6, R, VV, UH, timed_out, consumed, issued_end,  \
                                            pol)) {                                                         \
         aborted = true;                                                                                    \
         break;                                                                                             \
