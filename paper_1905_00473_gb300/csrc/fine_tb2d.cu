@@ -57,31 +57,18 @@ using namespace tb;
 
 constexpr int kCpt = 4;   // columns per thread
 constexpr int kPre = 2;   // rows requested ahead of the consumer
-constexpr int kU = 12;    // rows of the kappa/D0 ring
+constexpr int kU = 12;    // rows of the kappa/D0 ring, and the unroll of the row loop
 constexpr int kRS = 6;    // rows of the u_hi / u_t / residual ring
-#ifndef PR_TB2D_UNROLL
-#define PR_TB2D_UNROLL 12
-#endif
-constexpr int kUnroll = PR_TB2D_UNROLL;   // pipeline steps per loop iteration: 6 or 12
-static_assert(kUnroll == 6 || kUnroll == 12, "the unroll is one or two half-laps of the kappa/D0 ring");
-static_assert(kUnroll % 3 == 0 && kUnroll % kRS == 0, "the small ring periods must divide the unroll");
+static_assert(kU % 3 == 0 && kU % kRS == 0, "the small ring periods must divide the unroll");
 
 // Deep-ring slot of the row at static offset c from ring position q, with
-// kc = (q mod kUnroll) + c (a constant once the loops are unrolled) and h6 =
-// 6 ((q / 6) mod 2) when the unroll is 6 (0 when it is 12): slot
-// (kc + h6) mod 12, which is base +- h6 rows plus a constant offset.
-__device__ __forceinline__ uint32_t dslot(int kc, uint32_t h6) {
-    const uint32_t s = (uint32_t)((kc + 2 * kU) % kU);
-    return s < 6 ? s + h6 : s - h6;
-}
-static_assert(kRS >= kPre + 3, "the shallow ring holds rows q-2 .. q+kPre");
+// kc = (q mod kU) + c a constant once the loops are unrolled.
+__device__ __forceinline__ constexpr uint32_t dslot(int kc) { return (uint32_t)((kc + 2 * kU) % kU); }
 
 // Shared memory of one CTA.  Every ring slot, mbarrier and x-edge buffer of
-// the pipeline step that handles ring position q is (q mod its ring size):
-// inside the kUnroll-fold unrolled loop a compile-time constant (the small
-// rings, the register rings) or a constant offset from one of two uniform
-// bases (the 12-row deep ring, dslot), because every segment starts at a
-// ring position that is a multiple of kUnroll.
+// the pipeline step that handles ring position q is (q mod its ring size), a
+// compile-time constant inside the kU-fold unrolled loop, because every
+// segment starts at a ring position that is a multiple of kU.
 template <int NT, int B>
 struct Smem {
     static_assert(kU >= B + kPre + 1, "the kappa/D0 ring holds rows q-B .. q+kPre");
@@ -138,8 +125,7 @@ __device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, un
     }
 }
 
-// One pipeline step at ring position q = sg.base + i with K = q mod kUnroll
-// and h6 = 6 ((q / 6) mod 2) for a 6-fold unroll (else 0).
+// One pipeline step at ring position q = sg.base + i with K = q mod kU.
 // Register rings per level l (period 3, K mod 3 selects the slots):
 //   R[l][.]  du rows of level l's input: centre = K%3, south = (K+2)%3,
 //            north = (K+1)%3 (written this step by the level below)
@@ -148,8 +134,8 @@ __device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, un
 // when some thread's bounded wait gave up.
 template <int NT, int B, int XH, bool MID, bool HALF0, int K>
 __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, unsigned char* sm, int i,
-                                          uint32_t par, uint32_t h6, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
-                                          float (&UH)[3][kCpt],
+                                          uint32_t par, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
+                                          float (&UH)[3][kCpt], float (&KR)[kU][kCpt],
                                           int& timed_out, uint32_t& consumed, uint32_t& issued_end,
                                           const Pols& pol) {
     using S = Smem<NT, B>;
@@ -163,7 +149,7 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
 
     // ---- producer: row i + kPre into the rings ---------------------------
     if (t == 0 && i + kPre < sg.nload) {
-        issue_row<NT, B, XH>(p, sg, sm, i + kPre, dslot(K + kPre, h6), SN, pol);
+        issue_row<NT, B, XH>(p, sg, sm, i + kPre, dslot(K + kPre), SN, pol);
         issued_end = sg.base + (uint32_t)(i + kPre + 1);
     }
 
@@ -183,7 +169,7 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
     float d0n[kCpt] = {0.f, 0.f, 0.f, 0.f};
     const bool have_row = i < sg.nload;
     if (have_row) {
-        if (!timed_out && !mbar_wait_bounded(S::bar(sm, dslot(K, h6)), par, p.wait_ns)) {
+        if (!timed_out && !mbar_wait_bounded(S::bar(sm, dslot(K)), par, p.wait_ns)) {
             atomicExch(p.flag, 1);
             timed_out = 1;
         }
@@ -195,6 +181,16 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
         // holds row i), so D0 needs no shared loads for the thread's own columns
 #pragma unroll
         for (int k = 0; k < kCpt; ++k) UH[CUR][k] = uu[k];
+        // kappa of row i, read once: the B levels take it from a register ring
+        // of kU rows (slot K) at the next B steps.  x-strip CTAs, whose 260
+        // threads leave 168 registers a thread, read it per level instead.
+        if constexpr (XH == 0) {
+            const float4 kq = *(const float4*)((const float*)S::deep(sm, dslot(K)) + kCpt * t);
+            KR[K][0] = kq.x;
+            KR[K][1] = kq.y;
+            KR[K][2] = kq.z;
+            KR[K][3] = kq.w;
+        }
         if (sg.r_s) {
             const uint2 r2 = *(const uint2*)(s0 + W * 8 + 2 * kCpt * t);
             R[0][NXT][0] = pr_bf16_lo(r2.x);
@@ -247,7 +243,7 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
     float dout[kCpt], vout[kCpt];
 #pragma unroll
     for (int l = 0; l < B; ++l) {
-        const float* drow = (const float*)S::deep(sm, dslot(K - 1 - l, h6));
+        const float* drow = (const float*)S::deep(sm, dslot(K - 1 - l));
         float vin[kCpt];
         if (l == 0) {
             const float4 v4 = *(const float4*)(S::shal(sm, S1) + W * 4 + 16 * t);
@@ -258,8 +254,14 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
         }
         float dn[kCpt], vn[kCpt];
         if (MID || l < L) {
-            const float4 k4 = *(const float4*)(drow + kCpt * t);
-            float kk[4] = {k4.x, k4.y, k4.z, k4.w};
+            float kk[4];
+            if constexpr (XH == 0) {
+#pragma unroll
+                for (int k = 0; k < kCpt; ++k) kk[k] = KR[(K + 2 * kU - 1 - l) % kU][k];
+            } else {
+                const float4 k4 = *(const float4*)(drow + kCpt * t);
+                kk[0] = k4.x; kk[1] = k4.y; kk[2] = k4.z; kk[3] = k4.w;
+            }
             float dd[4];
             if (l == 0) {
 #pragma unroll
@@ -381,7 +383,7 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
         }
     }
     if (have_row && i >= 1) {
-        float* dd = (float*)S::deep(sm, dslot(K - 1, h6)) + W;
+        float* dd = (float*)S::deep(sm, dslot(K - 1)) + W;
         *(float4*)(dd + kCpt * t) = make_float4(d0n[0], d0n[1], d0n[2], d0n[3]);
     }
     // one barrier per row; it also makes the abort decision uniform
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     const int64_t r_begin = balanced_row(p.rows_total, n, L + B, blockIdx.x, gridDim.x);
     const int64_t r_end = balanced_row(p.rows_total, n, L + B, blockIdx.x + 1, gridDim.x);
     // ring positions: a segment occupies [base, base + niter) and the next one
-    // starts at the following multiple of kUnroll; positions that receive no
+    // starts at the following multiple of kU; positions that receive no
     // copy get a plain arrival, so slot s completes its phase j at position
     // j kU + s
     uint32_t pos = 0, consumed = 0, issued_end = 0;
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
             }
         }
 
-        float R[B][3][kCpt], VV[B][3][kCpt], UH[3][kCpt];
+        float R[B][3][kCpt], VV[B][3][kCpt], UH[3][kCpt], KR[kU][kCpt];
 #pragma unroll
         for (int l = 0; l < B; ++l)
 #pragma unroll
@@ -466,30 +468,30 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         for (int s = 0; s < 3; ++s)
 #pragma unroll
             for (int k = 0; k < kCpt; ++k) UH[s][k] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < kU; ++s)
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) KR[s][k] = 0.0f;
 
-        uint32_t lap6 = pos / 6;   // half-laps of the deep ring before this position
+        uint32_t par = (pos / kU) & 1u;   // phase parity of the current ring lap
         int i = 0;
 #define PR_TB2D_STEP(K)                                                                                   \
     if (i >= niter) break;                                                                                 \
-    if (tb2d_step<NT, B, XH, MID, HALF0, K>(p, sg, sm, i, par, h6, R, VV, UH, timed_out, consumed, issued_end,  \
+    if (tb2d_step<NT, B, XH, MID, HALF0, K>(p, sg, sm, i, par, R, VV, UH, KR, timed_out, consumed, issued_end,  \
                                            pol)) {                                                         \
         aborted = true;                                                                                    \
         break;                                                                                             \
     }                                                                                                      \
     ++i;
         for (;;) {
-            const uint32_t par = (lap6 >> 1) & 1u;
-            const uint32_t h6 = kUnroll == 6 ? (lap6 & 1u) * 6u : 0u;
             PR_TB2D_STEP(0) PR_TB2D_STEP(1) PR_TB2D_STEP(2) PR_TB2D_STEP(3) PR_TB2D_STEP(4) PR_TB2D_STEP(5)
-            if constexpr (kUnroll == 12) {
-                PR_TB2D_STEP(6) PR_TB2D_STEP(7) PR_TB2D_STEP(8) PR_TB2D_STEP(9) PR_TB2D_STEP(10) PR_TB2D_STEP(11)
-            }
-            lap6 += kUnroll / 6;
+            PR_TB2D_STEP(6) PR_TB2D_STEP(7) PR_TB2D_STEP(8) PR_TB2D_STEP(9) PR_TB2D_STEP(10) PR_TB2D_STEP(11)
+            par ^= 1u;
         }
 #undef PR_TB2D_STEP
         if (aborted) break;
         // close the lap: complete the phases of the positions that got no copy
-        const uint32_t next = (pos + (uint32_t)niter + kUnroll - 1) / kUnroll * kUnroll;
+        const uint32_t next = (pos + (uint32_t)niter + kU - 1) / kU * kU;
         if (t == 0)
             for (uint32_t q = pos + (uint32_t)sg.nload; q < next; ++q) mbar_arrive(S::bar(sm, q % kU));
         pos = next;
