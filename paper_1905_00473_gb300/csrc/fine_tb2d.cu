@@ -135,7 +135,7 @@ __device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, un
 template <int NT, int B, int XH, bool MID, bool HALF0, int K>
 __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, unsigned char* sm, int i,
                                           uint32_t par, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
-                                          float (&UH)[3][kCpt], float (&KR)[kU][kCpt],
+                                          float (&UH)[3][kCpt], float (&KR)[kU][kCpt], float (&DR)[kU][kCpt],
                                           int& timed_out, uint32_t& consumed, uint32_t& issued_end,
                                           const Pols& pol) {
     using S = Smem<NT, B>;
@@ -266,6 +266,9 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
             if (l == 0) {
 #pragma unroll
                 for (int k = 0; k < kCpt; ++k) dd[k] = d0n[k];
+            } else if constexpr (MID && XH == 0) {
+#pragma unroll
+                for (int k = 0; k < kCpt; ++k) dd[k] = DR[(K + 2 * kU - 1 - l) % kU][k];
             } else {
                 const float4 d4 = *(const float4*)(drow + W + kCpt * t);
                 dd[0] = d4.x; dd[1] = d4.y; dd[2] = d4.z; dd[3] = d4.w;
@@ -383,8 +386,15 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
         }
     }
     if (have_row && i >= 1) {
-        float* dd = (float*)S::deep(sm, dslot(K - 1)) + W;
-        *(float4*)(dd + kCpt * t) = make_float4(d0n[0], d0n[1], d0n[2], d0n[3]);
+        // D0 of row i-1 for levels 1..B-1 at the next steps: a register ring
+        // of kU rows in the middle-pass kernel (whole rows), else the deep ring
+        if constexpr (MID && XH == 0) {
+#pragma unroll
+            for (int k = 0; k < kCpt; ++k) DR[(K + kU - 1) % kU][k] = d0n[k];
+        } else {
+            float* dd = (float*)S::deep(sm, dslot(K - 1)) + W;
+            *(float4*)(dd + kCpt * t) = make_float4(d0n[0], d0n[1], d0n[2], d0n[3]);
+        }
     }
     // one barrier per row; it also makes the abort decision uniform
     return __syncthreads_or(timed_out) != 0;
@@ -457,7 +467,7 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
             }
         }
 
-        float R[B][3][kCpt], VV[B][3][kCpt], UH[3][kCpt], KR[kU][kCpt];
+        float R[B][3][kCpt], VV[B][3][kCpt], UH[3][kCpt], KR[kU][kCpt], DR[kU][kCpt];
 #pragma unroll
         for (int l = 0; l < B; ++l)
 #pragma unroll
@@ -471,14 +481,14 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
 #pragma unroll
         for (int s = 0; s < kU; ++s)
 #pragma unroll
-            for (int k = 0; k < kCpt; ++k) KR[s][k] = 0.0f;
+            for (int k = 0; k < kCpt; ++k) KR[s][k] = DR[s][k] = 0.0f;
 
         uint32_t par = (pos / kU) & 1u;   // phase parity of the current ring lap
         int i = 0;
 #define PR_TB2D_STEP(K)                                                                                   \
     if (i >= niter) break;                                                                                 \
-    if (tb2d_step<NT, B, XH, MID, HALF0, K>(p, sg, sm, i, par, R, VV, UH, KR, timed_out, consumed, issued_end,  \
-                                           pol)) {                                                         \
+    if (tb2d_step<NT, B, XH, MID, HALF0, K>(p, sg, sm, i, par, R, VV, UH, KR, DR, timed_out, consumed,          \
+                                           issued_end, pol)) {                                             \
         aborted = true;                                                                                    \
         break;                                                                                             \
     }                                                                                                      \
