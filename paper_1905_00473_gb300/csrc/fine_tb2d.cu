@@ -12,8 +12,15 @@
 // one kick+drift, and row i-B leaves the pipeline finished.  A level needs
 // its own column's rows above/below (registers) and the x-neighbours of its
 // edge columns, which come from the neighbouring threads through a small
-// triple-buffered shared array written by the level below one iteration
-// earlier.  One barrier per row.
+// double-buffered shared array written one iteration earlier (in middle
+// passes the edges of four levels travel as one 16-byte vector).  One barrier
+// per row.
+//
+// Register rings.  What a thread reads again for its own columns stays in
+// registers: the du and u_t rows of every level, u_hi of the last three rows
+// (for D0), and, in whole-row CTAs, kappa of the last 12 rows (read from
+// shared memory once, when the row arrives) and, in middle passes, D0 of the
+// last 12 rows.
 //
 // Loads.  One elected thread streams rows with cp.async.bulk (TMA bulk
 // copies: rows are contiguous and 16-byte aligned) into shared-memory rings
@@ -24,8 +31,8 @@
 // and all its threads leave the loop together.
 //
 // Static rings.  The row loop is unrolled 12-fold, the kappa/D0 ring depth,
-// which the shallow ring (6), the x-edge buffers (3) and the register rings
-// (3) divide.  Every segment starts at a ring position that is a multiple of
+// which the shallow ring (6), the x-edge buffers (2) and the register rings
+// (3, 12) divide.  Every segment starts at a ring position that is a multiple of
 // 12, so each unrolled step addresses its slots, mbarriers and buffers at
 // compile-time offsets; positions that receive no copy (drain steps, the
 // padding to the next multiple of 12) get a plain mbarrier arrival, so slot s
@@ -77,7 +84,12 @@ struct Smem {
     static constexpr uint32_t sh_row = 10u * W;                  // u_hi W | u_t W (float) | r W (bf16)
     static constexpr uint32_t deep_bytes = kU * deep_row;
     static constexpr uint32_t sh_bytes = kRS * sh_row;
-    static constexpr uint32_t xbuf_bytes = 3u * B * 2 * NT * 4;  // [3][B][left|right][NT]
+    // x-edge exchange, double-buffered.  Middle passes: [2][left|right][NQ][NT]
+    // float4, the edges of levels 4q..4q+3 of a thread in one 16-byte vector;
+    // the general variant: [2][B][left|right][NT] float.
+    static constexpr int NQ = (B + 3) / 4;
+    static constexpr uint32_t xq_bytes = 2u * 2 * NQ * NT * 16, xs_bytes = 2u * B * 2 * NT * 4;
+    static constexpr uint32_t xbuf_bytes = xq_bytes > xs_bytes ? xq_bytes : xs_bytes;
     static constexpr uint32_t bar_bytes = kU * 8;
     static constexpr uint32_t total = deep_bytes + sh_bytes + xbuf_bytes + bar_bytes;
     static_assert(deep_row % 16 == 0 && sh_row % 16 == 0 && (W * 4) % 16 == 0,
@@ -86,7 +98,10 @@ struct Smem {
     __device__ static unsigned char* shal(unsigned char* sm, uint32_t slot) {
         return sm + deep_bytes + slot * sh_row;
     }
-    __device__ static float* xbuf(unsigned char* sm, uint32_t buf) {
+    __device__ static float4* xbuf4(unsigned char* sm, uint32_t buf) {
+        return (float4*)(sm + deep_bytes + sh_bytes) + buf * (2 * NQ * NT);
+    }
+    __device__ static float* xbuf1(unsigned char* sm, uint32_t buf) {
         return (float*)(sm + deep_bytes + sh_bytes) + buf * (B * 2 * NT);
     }
     __device__ static uint64_t* bar(unsigned char* sm, uint32_t slot) {
@@ -237,13 +252,21 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
     }
 
     // ---- levels: level l advances row i-1-l ------------------------------
-    const float* xr = S::xbuf(sm, PRV);
+    // the neighbours' edges of the previous step: in the middle-pass kernel
+    // one quad of levels per 128-bit load, else one level per scalar load
+    const float4* xr4 = S::xbuf4(sm, (K & 1) ^ 1);
+    const float* xr1 = S::xbuf1(sm, (K & 1) ^ 1);
     const int tl = (t + NT - 1) % NT, tr = (t + 1) % NT;
+    float4 xlq, xrq;   // right edges of thread t-1, left edges of thread t+1
     const float dt = p.dt;
     float dout[kCpt], vout[kCpt];
 #pragma unroll
     for (int l = 0; l < B; ++l) {
         const float* drow = (const float*)S::deep(sm, dslot(K - 1 - l));
+        if (MID && l % 4 == 0) {
+            xlq = xr4[(1 * S::NQ + l / 4) * NT + tl];
+            xrq = xr4[(0 * S::NQ + l / 4) * NT + tr];
+        }
         float vin[kCpt];
         if (l == 0) {
             const float4 v4 = *(const float4*)(S::shal(sm, S1) + W * 4 + 16 * t);
@@ -273,8 +296,14 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
                 const float4 d4 = *(const float4*)(drow + W + kCpt * t);
                 dd[0] = d4.x; dd[1] = d4.y; dd[2] = d4.z; dd[3] = d4.w;
             }
-            const float xl = xr[l * 2 * NT + NT + tl];
-            const float xrt = xr[l * 2 * NT + tr];
+            float xl, xrt;
+            if constexpr (MID) {
+                xl = l % 4 == 0 ? xlq.x : l % 4 == 1 ? xlq.y : l % 4 == 2 ? xlq.z : xlq.w;
+                xrt = l % 4 == 0 ? xrq.x : l % 4 == 1 ? xrq.y : l % 4 == 2 ? xrq.z : xrq.w;
+            } else {
+                xl = xr1[l * 2 * NT + NT + tl];
+                xrt = xr1[l * 2 * NT + tr];
+            }
             bool dr = true;
             if (MID && HALF0 && l == 0) {   // the first pass: level 0 is g = 0
 #pragma unroll
@@ -377,12 +406,28 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
     }
 
     // ---- shared stores, read only in later steps ----------------------------
-    float* xw = S::xbuf(sm, CUR);
+    if constexpr (MID) {
+        float4* xw = S::xbuf4(sm, K & 1);
 #pragma unroll
-    for (int l = 0; l < B; ++l) {
-        if (MID || l < L) {   // level l's input rows: edges read by level l next step
-            xw[l * 2 * NT + t] = R[l][NXT][0];
-            xw[l * 2 * NT + NT + t] = R[l][NXT][kCpt - 1];
+        for (int q = 0; q < S::NQ; ++q) {   // level l's input rows: edges read by level l next step
+            float e0[4], e1[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int l = 4 * q + j < B ? 4 * q + j : B - 1;
+                e0[j] = R[l][NXT][0];
+                e1[j] = R[l][NXT][kCpt - 1];
+            }
+            xw[(0 * S::NQ + q) * NT + t] = make_float4(e0[0], e0[1], e0[2], e0[3]);
+            xw[(1 * S::NQ + q) * NT + t] = make_float4(e1[0], e1[1], e1[2], e1[3]);
+        }
+    } else {
+        float* xw = S::xbuf1(sm, K & 1);
+#pragma unroll
+        for (int l = 0; l < B; ++l) {
+            if (l < L) {   // level l's input rows: edges read by level l next step
+                xw[l * 2 * NT + t] = R[l][NXT][0];
+                xw[l * 2 * NT + NT + t] = R[l][NXT][kCpt - 1];
+            }
         }
     }
     if (have_row && i >= 1) {
