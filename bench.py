@@ -160,12 +160,27 @@ def measured_peak() -> tuple[float, str]:
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = ("paper_1905_00473_gb300/csrc/fine_tb2d.cu", "paper_1905_00473_gb300/csrc/tb_common.cuh",
+                  "paper_1905_00473_gb300/csrc/pr_internal.cuh")
+
+
+def code_only(text: str) -> str:
+    """C/C++ source without comments and with whitespace collapsed, so that an
+    edit of comments alone keeps the hash of the code."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_source_hash(read=None) -> str:
+    """Hash of the fused kernel's code (comments excluded); `read(rel)` returns
+    a file's text (default: the working tree)."""
+    if read is None:
+        read = lambda rel: open(os.path.join(ROOT, rel)).read()  # noqa: E731
     h = hashlib.sha256()
-    for rel in ("paper_1905_00473_gb300/csrc/fine_tb2d.cu", "paper_1905_00473_gb300/csrc/tb_common.cuh",
-                "paper_1905_00473_gb300/csrc/pr_internal.cuh"):
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+    for rel in KERNEL_SOURCES:
+        h.update(code_only(read(rel)).encode())
     return h.hexdigest()[:16]
 
 

@@ -24,9 +24,10 @@
 //
 // Loads.  One elected thread streams rows with cp.async.bulk (TMA bulk
 // copies: rows are contiguous and 16-byte aligned) into shared-memory rings
-// guarded by one mbarrier per row slot: kappa into a 12-row ring that also
-// holds D0 (below) for the rows in flight, u_hi, u_t and the bfloat16
-// residual into a 6-row ring.  The finished row re-reads its u_hi from L2.
+// guarded by one mbarrier per row slot: kappa into a 12-row ring (whose other
+// half holds D0 where D0 is not kept in registers), u_hi, u_t and the
+// bfloat16 residual into a 6-row ring.  The finished row re-reads its u_hi
+// from L2.
 // Waits are bounded: after ~2 s the CTA records PR_ETIMEOUT in a device flag
 // and all its threads leave the loop together.
 //
