@@ -79,7 +79,7 @@ __global__ void adj_level(const T* __restrict__ lu, const T* __restrict__ lv, co
 // (n % 4 == 0): 128-bit quads of every field and of its y/z neighbours
 // (grid_rows.cuh), the same arithmetic in the same order per point.
 template <int DIM>
-__global__ void fwd_level_x4(const float* __restrict__ u, float* __restrict__ v, float* __restrict__ un,
+__global__ void __launch_bounds__(256, 4) fwd_level_x4(const float* __restrict__ u, float* __restrict__ v, float* __restrict__ un,
                              const float* __restrict__ kap, int64_t n, int64_t pts, float w, float dt, int drift) {
     typedef rows::Quad<DIM, float, float4> Q;
     const int64_t x0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
@@ -108,7 +108,7 @@ __global__ void fwd_level_x4(const float* __restrict__ u, float* __restrict__ v,
 }
 
 template <int DIM>
-__global__ void adj_level_x4(const float* __restrict__ lu, const float* __restrict__ lv,
+__global__ void __launch_bounds__(256) adj_level_x4(const float* __restrict__ lu, const float* __restrict__ lv,
                              const float* __restrict__ ug, const float* __restrict__ kap,
                              float* __restrict__ lu_o, float* __restrict__ lv_o, double* __restrict__ gk,
                              int64_t n, int64_t pts, float w, float dt, int drift) {

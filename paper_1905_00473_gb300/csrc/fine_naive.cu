@@ -77,8 +77,9 @@ template <typename RT> struct ResidVec;
 template <> struct ResidVec<int8_t> { typedef char4 type; };
 template <> struct ResidVec<uint16_t> { typedef ushort4 type; };
 
+// (at least 4 blocks per SM: 32 warps to keep enough loads in flight)
 template <int DIM, typename RT>
-__global__ void __launch_bounds__(256) level_f32_x4(
+__global__ void __launch_bounds__(256, 4) level_f32_x4(
     const float* __restrict__ u, const RT* __restrict__ r, const float* __restrict__ v,
     const float* __restrict__ kap, float* __restrict__ uo, RT* __restrict__ ro,
     float* __restrict__ vo, int64_t n, int64_t pts, int64_t total_rows, float wk, float dt, int drift) {
