@@ -60,10 +60,11 @@ typedef struct pr_grid {
 } pr_grid;
 
 /* Options.  block_depth: fine steps fused per HBM pass of the 2D FP32 kernel
- * (0 = library default: 8, or 4 where the width has no depth-8 kernel;
- * 8 or 4 use the fused kernel where it applies: n = 128, 256, 512, 1024, and
- * 2048 at depth 4 only; 1 = one step per pass).  Other fields are reserved
- * for the coarse/correction stages and are ignored by the fine path. */
+ * (0 = library default: 8; 8 or 4 use the fused kernel where it applies:
+ * n = 128, 256, 512, 1024 and 2048, whose rows are shared by a two-CTA
+ * cluster at depth 8 and split into x-strips at depth 4; 1 = one step per
+ * pass).  Other fields are reserved for the coarse/correction stages and are
+ * ignored by the fine path. */
 typedef struct pr_options {
     int dtype;          /* pr_dtype */
     int grad_order;     /* 2, 4, 6, 8 or 0 = spectral (nabla_h, Sec. 6.4) */
@@ -240,7 +241,7 @@ void pr_batch_destroy(pr_batch* b);
 /* pr_set_fused_columns -- thread geometry of the fused 2D FP32 passes of
  * this context: 2 or 4 grid columns per thread (n/2 or n/4 threads per row),
  * or 0 = the default (4, the faster geometry on a GB300 at n = 512 and 1024;
- * n = 2048 always runs four columns in x-strips).  Both compute the same level
+ * n = 2048 always runs four columns).  Both compute the same level
  * recurrence; results agree to rounding.  PR_EINVAL for any other value.
  * Takes effect at the next call. */
 pr_status pr_set_fused_columns(pr_ctx* ctx, int columns);

@@ -16,11 +16,23 @@
 // passes the edges of four levels travel as one 16-byte vector).  One barrier
 // per row.
 //
+// Cluster rows (n = 2048 at depth 8).  A row is shared by the two CTAs of a
+// thread-block cluster, each holding one half.  The threads at the ends of a
+// half-row store their wrap-around x-edges into the partner's edge buffer
+// with st.async, which completes transaction bytes on an mbarrier there;
+// the partner's opposite end thread waits for them (bounded) and then reads
+// its own buffer exactly as a whole-row CTA does.  No CTA reads the other's
+// shared memory and there is no cluster barrier per row: a CTA can run at
+// most one step ahead of its partner, which the double-buffered edges allow.
+// D0 at the ends takes the u_hi columns beyond the half-row from a 16-byte
+// bulk copy per side.  Cluster barriers at entry and exit (after the last
+// pushes have landed) bracket the exchange.
+//
 // Register rings.  What a thread reads again for its own columns stays in
 // registers: the du and u_t rows of every level, u_hi of the last three rows
 // (for D0), and, in whole-row CTAs, kappa of the last 12 rows (read from
-// shared memory once, when the row arrives) and, in middle passes, D0 of the
-// last 12 rows.
+// shared memory once, when the row arrives) and, in middle passes of
+// CTAs that hold whole rows alone, D0 of the last 12 rows.
 //
 // Loads.  One elected thread streams rows with cp.async.bulk (TMA bulk
 // copies: rows are contiguous and 16-byte aligned) into shared-memory rings
@@ -91,8 +103,12 @@ struct Smem {
     static constexpr int NQ = (B + 3) / 4;
     static constexpr uint32_t xq_bytes = 2u * 2 * NQ * NT * 16, xs_bytes = 2u * B * 2 * NT * 4;
     static constexpr uint32_t xbuf_bytes = xq_bytes > xs_bytes ? xq_bytes : xs_bytes;
-    static constexpr uint32_t bar_bytes = kU * 8;
-    static constexpr uint32_t total = deep_bytes + sh_bytes + xbuf_bytes + bar_bytes;
+    // cluster rows: the u_hi columns just outside the half-row (4 each side)
+    // per shallow slot, and the exchange mbarriers, one per (step parity b,
+    // end s: 0 = thread 0, 1 = thread NT-1, part q = levels 4q..4q+3)
+    static constexpr uint32_t halo_bytes = kRS * 2 * 16;
+    static constexpr uint32_t bar_bytes = (kU + 2 * 2 * NQ) * 8;   // ring slots, then the exchange
+    static constexpr uint32_t total = deep_bytes + sh_bytes + xbuf_bytes + halo_bytes + bar_bytes;
     static_assert(deep_row % 16 == 0 && sh_row % 16 == 0 && (W * 4) % 16 == 0,
                   "bulk-copy destinations must stay 16-byte aligned");
     __device__ static unsigned char* deep(unsigned char* sm, uint32_t slot) { return sm + slot * deep_row; }
@@ -105,32 +121,84 @@ struct Smem {
     __device__ static float* xbuf1(unsigned char* sm, uint32_t buf) {
         return (float*)(sm + deep_bytes + sh_bytes) + buf * (B * 2 * NT);
     }
-    __device__ static uint64_t* bar(unsigned char* sm, uint32_t slot) {
-        return (uint64_t*)(sm + deep_bytes + sh_bytes + xbuf_bytes) + slot;
+    __device__ static float4* halo(unsigned char* sm, uint32_t slot, uint32_t side) {
+        return (float4*)(sm + deep_bytes + sh_bytes + xbuf_bytes) + slot * 2 + side;
     }
+    __device__ static uint64_t* bar(unsigned char* sm, uint32_t slot) {
+        return (uint64_t*)(sm + deep_bytes + sh_bytes + xbuf_bytes + halo_bytes) + slot;
+    }
+    __device__ static uint64_t* ebar(unsigned char* sm, uint32_t b, uint32_t s, uint32_t q) {
+        return bar(sm, kU + (b * 2 + s) * NQ + q);
+    }
+    static constexpr uint32_t part_tx = 16;   // bytes pushed per part and step
 };
 
 struct Pols {
     uint64_t first, last, norm;   // L2 evict-first (streamed), evict-last (kappa), normal (u_hi)
 };
 
+// Rows shared by the two CTAs of a cluster (n = 8 NT): the count of steps
+// this CTA has finished, the same in both CTAs because they walk the same
+// segments.
+struct Pair {
+    uint32_t step;
+};
+
+// Cluster-row exchange.  The end threads of a half-row (t = 0 and NT-1)
+// write their wrap-around x-edge entries (thread 0's left edges, thread
+// NT-1's right edges) into the partner's x-edge buffer, at the same offset,
+// instead of their own: each entry is then read by the partner's opposite
+// end thread exactly as a whole-row CTA reads its own.  A push of part q
+// (the edges of levels 4q..4q+3 of global step g) completes 16 bytes on the
+// partner's mbarrier (g & 1, receiving end, q).  The receiving thread waits
+// for phase ((g-1) >> 1) & 1 before reading part q at step g and re-arms
+// the mbarrier (one arrival with 16 expected bytes) for step g+1.
+template <int NT, int B>
+__device__ __forceinline__ bool rx_wait(unsigned char* sm, uint32_t g, int q, uint64_t limit_ns) {
+    using S = Smem<NT, B>;
+    const uint32_t side = threadIdx.x == 0 ? 0u : 1u;
+    return mbar_wait_bounded(S::ebar(sm, (g - 1) & 1u, side, q), ((g - 1) >> 1) & 1u, limit_ns);
+}
+template <int NT, int B>
+__device__ __forceinline__ void rx_rearm(unsigned char* sm, uint32_t g, int q) {
+    using S = Smem<NT, B>;
+    const uint32_t side = threadIdx.x == 0 ? 0u : 1u;
+    mbar_expect_tx(S::ebar(sm, (g - 1) & 1u, side, q), S::part_tx);
+}
+// the partner's mbarrier that a push of part q at step g completes
+template <int NT, int B>
+__device__ __forceinline__ uint32_t tx_bar(unsigned char* sm, uint32_t g, int q, uint32_t prank) {
+    using S = Smem<NT, B>;
+    const uint32_t side = threadIdx.x == 0 ? 1u : 0u;   // received by the partner's opposite end
+    return mapa_rank(smem_u32(S::ebar(sm, g & 1u, side, q)), prank);
+}
+
 // Request local row rho of the segment (kappa, u_hi, u_t, residual) into the
 // deep slot DS and the shallow slot SS; called by one thread.
-template <int NT, int B, int XH>
+template <int NT, int B, int XH, int CL>
 __device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, unsigned char* sm, int rho,
                                           uint32_t DS, uint32_t SS, const Pols& pol) {
     using S = Smem<NT, B>;
     constexpr int W = S::W;
     const int n = p.n;
-    const int64_t off = (int64_t)seg_row(sg.ylo, rho, n) * n;
+    // whole rows start at column 0; a cluster CTA's part of a row at x0
+    const int64_t off = (int64_t)seg_row(sg.ylo, rho, n) * n + (CL > 1 ? sg.x0 : 0);
     uint64_t* bar = S::bar(sm, DS);
     unsigned char* drow = S::deep(sm, DS);
     unsigned char* srow = S::shal(sm, SS);
     constexpr uint32_t row_bytes = (uint32_t)W * 4;
-    mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)W * 2 : 0u) + p.tx_extra);
+    mbar_expect_tx(bar, 3 * row_bytes + (sg.r_s ? (uint32_t)W * 2 : 0u) + (CL > 1 ? 32u : 0u) + p.tx_extra);
     if (XH == 0) {
         bulk_g2s(drow, p.kap + off, row_bytes, bar, pol.last);
         bulk_g2s(srow, sg.u_s + off, row_bytes, bar, pol.norm);
+        if (CL > 1) {
+            // u_hi columns x0-4..x0-1 and x0+W..x0+W+3 (periodic), for D0 at
+            // the ends of the half-row
+            const int64_t row0 = off - sg.x0;
+            const int xl = sg.x0 == 0 ? n - 4 : sg.x0 - 4, xr = sg.x0 + W == n ? 0 : sg.x0 + W;
+            bulk_g2s(S::halo(sm, SS, 0), sg.u_s + row0 + xl, 16u, bar, pol.norm);
+            bulk_g2s(S::halo(sm, SS, 1), sg.u_s + row0 + xr, 16u, bar, pol.norm);
+        }
         bulk_g2s(srow + W * 4, sg.v_s + off, row_bytes, bar, pol.first);
         if (sg.r_s) bulk_g2s(srow + W * 8, sg.r_s + off, (uint32_t)W * 2, bar, pol.first);
     } else {
@@ -148,12 +216,12 @@ __device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, un
 //   VV[l][.] u_t of level l's input row: read (K+2)%3, written K%3
 // `par` is the mbarrier phase parity of the current ring lap.  Returns true
 // when some thread's bounded wait gave up.
-template <int NT, int B, int XH, bool MID, bool HALF0, int K>
+template <int NT, int B, int XH, bool MID, bool HALF0, int CL, int K>
 __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, unsigned char* sm, int i,
                                           uint32_t par, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
                                           float (&UH)[3][kCpt], float (&KR)[kU][kCpt], float (&DR)[kU][kCpt],
                                           int& timed_out, uint32_t& consumed, uint32_t& issued_end,
-                                          const Pols& pol) {
+                                          const Pols& pol, Pair& pr) {
     using S = Smem<NT, B>;
     constexpr int W = S::W;
     constexpr int CUR = K % 3, PRV = (K + 2) % 3, NXT = (K + 1) % 3;
@@ -165,8 +233,26 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
 
     // ---- producer: row i + kPre into the rings ---------------------------
     if (t == 0 && i + kPre < sg.nload) {
-        issue_row<NT, B, XH>(p, sg, sm, i + kPre, dslot(K + kPre), SN, pol);
+        issue_row<NT, B, XH, CL>(p, sg, sm, i + kPre, dslot(K + kPre), SN, pol);
         issued_end = sg.base + (uint32_t)(i + kPre + 1);
+    }
+
+    // ---- cluster rows: the partner's edges of the previous step have landed
+    const bool xend = CL > 1 && (t == 0 || t == NT - 1);   // the ends of the half-row
+    if constexpr (CL > 1) {
+        if (xend && pr.step > 0 && !timed_out) {
+#pragma unroll
+            for (int q = 0; q < S::NQ; ++q) {
+                if (!timed_out) {
+                    if (rx_wait<NT, B>(sm, pr.step, q, p.wait_ns)) {
+                        rx_rearm<NT, B>(sm, pr.step, q);
+                    } else {
+                        atomicExch(p.flag, 1);
+                        timed_out = 1;
+                    }
+                }
+            }
+        }
     }
 
     // ---- the finished row's u_hi, fetched early from L2 ------------------
@@ -224,7 +310,11 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
             const float* s1 = (const float*)S::shal(sm, S1);
             const float c[4] = {UH[PRV][0], UH[PRV][1], UH[PRV][2], UH[PRV][3]};
             const float s2v[4] = {UH[NXT][0], UH[NXT][1], UH[NXT][2], UH[NXT][3]};
-            const float xl = s1[(kCpt * t + W - 1) % W], xrr = s1[(kCpt * t + kCpt) % W];
+            float xl, xrr;
+            if (CL > 1 && t == 0) xl = S::halo(sm, S1, 0)->w;
+            else xl = s1[(kCpt * t + W - 1) % W];
+            if (CL > 1 && t == NT - 1) xrr = S::halo(sm, S1, 1)->x;
+            else xrr = s1[(kCpt * t + kCpt) % W];
 #if PR_TB2D_PACKED
             // columns (0,1) and (2,3) as f32x2 pairs, the same operations per lane
             const f2_t cp[2] = {f2_pack(c[0], c[1]), f2_pack(c[2], c[3])};
@@ -290,7 +380,7 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
             if (l == 0) {
 #pragma unroll
                 for (int k = 0; k < kCpt; ++k) dd[k] = d0n[k];
-            } else if constexpr (MID && XH == 0) {
+            } else if constexpr (MID && XH == 0 && CL == 1) {
 #pragma unroll
                 for (int k = 0; k < kCpt; ++k) dd[k] = DR[(K + 2 * kU - 1 - l) % kU][k];
             } else {
@@ -305,6 +395,7 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
                 xl = xr1[l * 2 * NT + NT + tl];
                 xrt = xr1[l * 2 * NT + tr];
             }
+
             bool dr = true;
             if (MID && HALF0 && l == 0) {   // the first pass: level 0 is g = 0
 #pragma unroll
@@ -418,23 +509,50 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
                 e0[j] = R[l][NXT][0];
                 e1[j] = R[l][NXT][kCpt - 1];
             }
-            xw[(0 * S::NQ + q) * NT + t] = make_float4(e0[0], e0[1], e0[2], e0[3]);
-            xw[(1 * S::NQ + q) * NT + t] = make_float4(e1[0], e1[1], e1[2], e1[3]);
+            float4* d0 = xw + (0 * S::NQ + q) * NT + t;
+            float4* d1 = xw + (1 * S::NQ + q) * NT + t;
+            const float4 v0 = make_float4(e0[0], e0[1], e0[2], e0[3]), v1 = make_float4(e1[0], e1[1], e1[2], e1[3]);
+            if (CL > 1 && t == 0) {
+                // cluster rows: the wrap-around entry goes to the partner
+                const uint32_t prank = cluster_rank() ^ 1u;
+                st_async_f4(mapa_rank(smem_u32(d0), prank), v0, tx_bar<NT, B>(sm, pr.step, q, prank));
+            } else {
+                *d0 = v0;
+            }
+            if (CL > 1 && t == NT - 1) {
+                const uint32_t prank = cluster_rank() ^ 1u;
+                st_async_f4(mapa_rank(smem_u32(d1), prank), v1, tx_bar<NT, B>(sm, pr.step, q, prank));
+            } else {
+                *d1 = v1;
+            }
         }
     } else {
         float* xw = S::xbuf1(sm, K & 1);
 #pragma unroll
         for (int l = 0; l < B; ++l) {
-            if (l < L) {   // level l's input rows: edges read by level l next step
+            // cluster rows: the wrap-around entries go to the partner, every
+            // level (16 bytes per part and step)
+            if (CL > 1 && t == 0) {
+                const uint32_t prank = cluster_rank() ^ 1u;
+                st_async_f32(mapa_rank(smem_u32(xw + l * 2 * NT + t), prank), R[l][NXT][0],
+                             tx_bar<NT, B>(sm, pr.step, l / 4, prank));
+            } else if (l < L) {   // level l's input rows: edges read by level l next step
                 xw[l * 2 * NT + t] = R[l][NXT][0];
+            }
+            if (CL > 1 && t == NT - 1) {
+                const uint32_t prank = cluster_rank() ^ 1u;
+                st_async_f32(mapa_rank(smem_u32(xw + l * 2 * NT + NT + t), prank), R[l][NXT][kCpt - 1],
+                             tx_bar<NT, B>(sm, pr.step, l / 4, prank));
+            } else if (l < L) {
                 xw[l * 2 * NT + NT + t] = R[l][NXT][kCpt - 1];
             }
         }
     }
+    if constexpr (CL > 1) ++pr.step;
     if (have_row && i >= 1) {
         // D0 of row i-1 for levels 1..B-1 at the next steps: a register ring
         // of kU rows in the middle-pass kernel (whole rows), else the deep ring
-        if constexpr (MID && XH == 0) {
+        if constexpr (MID && XH == 0 && CL == 1) {
 #pragma unroll
             for (int k = 0; k < kCpt; ++k) DR[(K + kU - 1) % kU][k] = d0n[k];
         } else {
@@ -450,8 +568,9 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
 // x-strips of 4 NT columns, of which the middle 4 NT - 2 XH are final (the
 // stencil's reach grows one column per level, so XH >= B), and the rows of a
 // slice are covered by n / (4 NT - 2 XH) strips.
-template <int NT, int B, int XH, bool MID, bool HALF0>
+template <int NT, int B, int XH, bool MID, bool HALF0, int CL>
 __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
+    static_assert(CL == 1 || (CL == 2 && XH == 0), "rows are shared by at most two CTAs, without x-strips");
     using S = Smem<NT, B>;
     extern __shared__ __align__(128) unsigned char sm[];
 
@@ -460,21 +579,42 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
     const int64_t pts = (int64_t)n * n;
     const int L = MID ? B : p.levels;
     // an earlier pass of this context gave up waiting: its results are not
-    // valid, skip the work until pr_check reports and clears the flag
-    if (*(volatile int*)p.flag) return;
+    // valid, skip the work until pr_check reports and clears the flag (a
+    // cluster CTA still meets its partner at the two cluster barriers)
+    const bool skip = *(volatile int*)p.flag != 0;
+    if (CL == 1 && skip) return;
 
     if (t == 0) {
         for (int s = 0; s < kU; ++s) mbar_init(S::bar(sm, s), 1);
+        if (CL > 1) {
+            // exchange barriers, armed for the partner's steps 0 and 1
+            for (uint32_t b = 0; b < 2; ++b)
+                for (uint32_t e = 0; e < 2; ++e)
+                    for (int q = 0; q < S::NQ; ++q) {
+                        mbar_init(S::ebar(sm, b, e, q), 1);
+                        mbar_expect_tx(S::ebar(sm, b, e, q), S::part_tx);
+                    }
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    Pair pr = {0u};
+    uint32_t rank = 0;
+    if constexpr (CL > 1) {
+        // both CTAs run and their mbarriers are initialised before either
+        // touches the other's shared memory
+        cluster_sync_all();
+        rank = cluster_rank();
+    }
     Pols pol = {0, 0, 0};
     if (t == 0) pol = {policy(0), policy(1), policy(2)};
 
-    // per-CTA row ranges of equal cost: rows + (L + B) steps per segment
-    const int64_t r_begin = balanced_row(p.rows_total, n, L + B, blockIdx.x, gridDim.x);
-    const int64_t r_end = balanced_row(p.rows_total, n, L + B, blockIdx.x + 1, gridDim.x);
+    // per-CTA (per-cluster) row ranges of equal cost: rows + (L + B) steps
+    // per segment
+    const int64_t unit = blockIdx.x / CL, units = gridDim.x / CL;
+    const int64_t r_begin = skip ? 0 : balanced_row(p.rows_total, n, L + B, unit, units);
+    const int64_t r_end = skip ? 0 : balanced_row(p.rows_total, n, L + B, unit + 1, units);
     // ring positions: a segment occupies [base, base + niter) and the next one
     // starts at the following multiple of kU; positions that receive no
     // copy get a plain arrival, so slot s completes its phase j at position
@@ -490,7 +630,7 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         Seg sg;
         const int64_t vslice = seg0 / n;
         const int64_t slice = vslice / strips;
-        sg.x0 = XH ? (int)(vslice - slice * strips) * kStripW - XH : 0;
+        sg.x0 = XH ? (int)(vslice - slice * strips) * kStripW - XH : (int)rank * S::W;
         const int ya = (int)(seg0 - vslice * n);
         const int64_t seg1 = min(r_end, (vslice + 1) * (int64_t)n);
         sg.H = (int)(seg1 - seg0);
@@ -504,11 +644,14 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         sg.base = pos;
         int ylo = (ya - L) % n;
         sg.ylo = ylo < 0 ? ylo + n : ylo;
-        const int niter = sg.H + L + B;
+        // cluster rows: an even step count, so that consecutive steps of
+        // consecutive segments alternate the x-edge buffers (ring positions
+        // restart at a multiple of kU), as the partner's pushes need
+        const int niter = sg.H + L + B + (CL > 1 ? ((sg.H + L + B) & 1) : 0);
 
         if (t == 0) {
             for (int rho = 0; rho < kPre && rho < sg.nload; ++rho) {
-                issue_row<NT, B, XH>(p, sg, sm, rho, (pos + (uint32_t)rho) % kU, (uint32_t)rho, pol);
+                issue_row<NT, B, XH, CL>(p, sg, sm, rho, (pos + (uint32_t)rho) % kU, (uint32_t)rho, pol);
                 issued_end = pos + (uint32_t)rho + 1;
             }
         }
@@ -533,8 +676,8 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         int i = 0;
 #define PR_TB2D_STEP(K)                                                                                   \
     if (i >= niter) break;                                                                                 \
-    if (tb2d_step<NT, B, XH, MID, HALF0, K>(p, sg, sm, i, par, R, VV, UH, KR, DR, timed_out, consumed,          \
-                                           issued_end, pol)) {                                             \
+    if (tb2d_step<NT, B, XH, MID, HALF0, CL, K>(p, sg, sm, i, par, R, VV, UH, KR, DR, timed_out, consumed,      \
+                                               issued_end, pol, pr)) {                                     \
         aborted = true;                                                                                    \
         break;                                                                                             \
     }                                                                                                      \
@@ -557,22 +700,54 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         for (uint32_t q = consumed; q < issued_end; ++q)
             (void)mbar_wait_bounded(S::bar(sm, q % kU), (q / kU) & 1u, p.wait_ns / 10);
     }
+    if constexpr (CL > 1) {
+        // The partner's pushes of its last step (and, after an abort, of the
+        // step after this CTA's last one) land before this CTA's shared
+        // memory is released: the end threads wait for them, bounded.
+        if ((t == 0 || t == NT - 1) && pr.step > 0) {
+            const int extra = aborted ? 2 : 1;
+            for (int e = 0; e < extra; ++e)
+                for (int q = 0; q < S::NQ; ++q)
+                    (void)rx_wait<NT, B>(sm, pr.step + (uint32_t)e, q, p.wait_ns / 10);
+        }
+        cluster_sync_all();
+    }
 }
 
-template <int NT, int B, int XH, bool MID, bool HALF0>
+// Launch of one pass.  CL = 2: clusters of two CTAs, each holding one half
+// of every row (n = 8 NT); the grid is as many clusters as fit at once.
+template <int NT, int B, int XH, bool MID, bool HALF0, int CL = 1>
 pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     using S = Smem<NT, B>;
-    auto kern = fine_tb2d_kernel<NT, B, XH, MID, HALF0>;
+    auto kern = fine_tb2d_kernel<NT, B, XH, MID, HALF0, CL>;
     static int configured_dev = -1;
-    static int blocks_per_sm = 0;
-    static int sms = 0;
+    static int units = 0;   // CTAs (CL = 1) or clusters resident at once
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = S::total;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (configured_dev != ctx->device) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::total);
         if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "tb2d: set shared memory size");
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, NT, S::total);
-        if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "tb2d: occupancy");
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-        if (blocks_per_sm < 1) return pr_fail(ctx, PR_ECUDA, "tb2d: kernel does not fit on an SM");
+        if (CL == 1) {
+            int blocks_per_sm = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, NT, S::total);
+            if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "tb2d: occupancy");
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+            units = blocks_per_sm * sms;
+        } else {
+            e = cudaOccupancyMaxActiveClusters(&units, kern, &cfg);
+            if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "tb2d: cluster occupancy");
+        }
+        if (units < 1) return pr_fail(ctx, PR_ECUDA, "tb2d: kernel does not fit on an SM");
         configured_dev = ctx->device;
     }
     Tb2dParams p;
@@ -593,10 +768,16 @@ pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     p.dt = (float)ctx->dt_f;
     p.tx_extra = ctx->debug_stall ? 16u : 0u;
     p.wait_ns = ctx->debug_stall ? 200000000ull : 2000000000ull;
-    int64_t grid = (int64_t)sms * blocks_per_sm;
+    int64_t grid = units;
     if (grid > p.rows_total) grid = p.rows_total;
-    kern<<<(int)grid, NT, S::total, st>>>(p);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (CL == 1) {
+        kern<<<(int)grid, NT, S::total, st>>>(p);
+        e = cudaGetLastError();
+    } else {
+        cfg.gridDim = dim3((unsigned)(grid * CL), 1, 1);
+        e = cudaLaunchKernelEx(&cfg, kern, p);
+    }
     if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "tb2d: launch");
     return PR_OK;
 }
@@ -605,12 +786,12 @@ pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
 // specialised kernel: the middle passes, and the first pass, which differs
 // only by the half kick at level 0 and no residual in.  The general variant
 // takes the rest (the last pass; passes of fewer levels).
-template <int NT, int B, int XH>
+template <int NT, int B, int XH, int CL = 1>
 pr_status launch_depth(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     const bool full = ps.levels == B && ps.g0 + B - 1 < ps.m && ps.r_out;
-    if (full && ps.g0 >= 1 && ps.r_in) return launch_cfg<NT, B, XH, true, false>(ctx, ps, st);
-    if (full && ps.g0 == 0 && !ps.r_in) return launch_cfg<NT, B, XH, true, true>(ctx, ps, st);
-    return launch_cfg<NT, B, XH, false, false>(ctx, ps, st);
+    if (full && ps.g0 >= 1 && ps.r_in) return launch_cfg<NT, B, XH, true, false, CL>(ctx, ps, st);
+    if (full && ps.g0 == 0 && !ps.r_in) return launch_cfg<NT, B, XH, true, true, CL>(ctx, ps, st);
+    return launch_cfg<NT, B, XH, false, false, CL>(ctx, ps, st);
 }
 
 template <int B>
@@ -631,12 +812,14 @@ pr_status launch_n(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
         case 256: return launch_depth<64, B, 0>(ctx, ps, st);
         case 512: return launch_depth<128, B, 0>(ctx, ps, st);
         case 1024: return launch_depth<256, B, 0>(ctx, ps, st);
-        // two x-strips of 1040 columns (1024 final + 8 each side) per row; 260
-        // threads are 9 warps, 3 on one SM sub-partition, which caps a thread
-        // at 168 registers: depth 4 fits, depth 8 would spill
+        // depth 8: every row is shared by a cluster of two CTAs of 256
+        // threads, which exchange the x-edges of the half-rows through
+        // distributed shared memory.  Depth 4: two x-strips of 1040 columns
+        // (1024 final + 8 each side) per row, 260 threads (9 warps, 3 on one
+        // SM sub-partition, at most 168 registers a thread).
         case 2048:
             if constexpr (B == 4) return launch_depth<260, B, 8>(ctx, ps, st);
-            else return pr_fail(ctx, PR_EINVAL, "tb2d: n = 2048 runs at depth 4");
+            else return launch_depth<256, B, 0, 2>(ctx, ps, st);
         default: return pr_fail(ctx, PR_EINVAL, "tb2d: unsupported grid size");
     }
 }
@@ -647,7 +830,7 @@ pr_status launch_n(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
 // shared-memory footprint; the batch autotuner chooses between them)
 bool pr_tb2d_supported(const pr_ctx* ctx, int depth) {
     if (ctx->dim != 2 || ctx->dtype != PR_F32 || (depth != 8 && depth != 4)) return false;
-    return ctx->n == 128 || ctx->n == 256 || ctx->n == 512 || ctx->n == 1024 || (ctx->n == 2048 && depth == 4);
+    return ctx->n == 128 || ctx->n == 256 || ctx->n == 512 || ctx->n == 1024 || ctx->n == 2048;
 }
 
 // whether a pass of block_depth + 1 levels can run fused (four columns per
@@ -667,8 +850,7 @@ pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     // geometry on a GB300 at n = 512 and 1024 as well (8 warps per SM, the
     // x-neighbour exchange and per-row overhead shared by four columns), and
     // two columns per thread (fine_tb2d_c2.cu, twice the warps) stays
-    // selectable.  n = 2048 runs in x-strips with four columns per thread
-    // whatever is set.
+    // selectable.  n = 2048 runs four columns per thread whatever is set.
     const int cols = ctx->tb_cols ? ctx->tb_cols : 4;
     if (cols == 2 && ctx->n <= 1024) return pr_launch_fine_tb2d_c2(ctx, ps, st);
     const int B = ctx->block_depth;

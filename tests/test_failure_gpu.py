@@ -10,12 +10,14 @@ from tests import _parity as P
 pytestmark = pytest.mark.gpu
 
 
-def test_bounded_wait_times_out_and_context_recovers(lib):
+@pytest.mark.parametrize("n", [256, 2048])   # whole rows per CTA; rows shared by a 2-CTA cluster
+def test_bounded_wait_times_out_and_context_recovers(lib, n):
     import time
     import torch
     from paper_1905_00473_gb300 import binding
-    w = W.custom_case(2, 256, 2, 7, "f32", "smooth")     # one fused pass of 8 levels
+    w = W.custom_case(2, n, 2, 7, "f32", "smooth")       # one fused pass of 8 levels
     ctx = P.make_ctx(w)
+    assert binding.pr_info(ctx)["block_depth"] == 8
     u, v = W.slice_states(w, seed=1)
     ud = torch.tensor(u, dtype=torch.float32, device="cuda")
     vd = torch.tensor(v, dtype=torch.float32, device="cuda")

@@ -55,15 +55,67 @@ def test_fused_2d_matches_oracle(lib, n, m_f, N, medium, cols):
 
 @pytest.mark.parametrize("m_f,N", [(9, 2), (4, 1)])
 def test_fused_2d_strips_2048(lib, m_f, N):
-    """n = 2048 runs in two x-strips of 1040 columns (8-column halo each side,
-    1024 final) at depth 4: passes of 4, 4, 2 levels (m_f = 9) or 4 + 1 levels
+    """n = 2048 at depth 4 runs in two x-strips of 1040 columns (8-column halo
+    each side, 1024 final): passes of 4, 4, 2 levels (m_f = 9) or 4 + 1 levels
     (m_f = 4), with rows of two slices and two strips split across the CTAs."""
     w = W.custom_case(2, 2048, N, m_f, "f32", "inclusion")
-    ctx = P.make_ctx(w)
+    ctx = P.make_ctx(w, block_depth=4)
     from paper_1905_00473_gb300 import binding
     assert binding.pr_info(ctx)["block_depth"] == 4
     u, v = W.slice_states(w, seed=11)
     _check_all(w, ctx, u, v)
+
+
+@pytest.mark.parametrize("m_f,N,passes", [
+    (20, 3, (3, 0)),   # 21 levels: first pass, middle pass, general pass of 5
+    (16, 2, (2, 1)),   # 17 levels: 8 + 8 fused, the final half kick alone
+    (7, 1, (1, 0)),    # 8 levels in one general pass (half kicks at both ends)
+])
+def test_fused_2d_cluster_rows_2048(lib, m_f, N, passes):
+    """n = 2048 at depth 8 (the default) shares every row between the two CTAs
+    of a thread-block cluster, which exchange the x-edges of their half-rows
+    through distributed shared memory.  The periodic wrap in x crosses from
+    one CTA to the other at both ends; rows of several slices are split
+    across the clusters."""
+    from paper_1905_00473_gb300 import binding
+    w = W.custom_case(2, 2048, N, m_f, "f32", "inclusion", seed=20 + m_f)
+    ctx = P.make_ctx(w)
+    assert binding.pr_info(ctx)["block_depth"] == 8
+    u, v = W.slice_states(w, seed=12)
+    binding.pr_profile(ctx, True)
+    _check_all(w, ctx, u, v)
+    binding.pr_profile(ctx, False)
+    assert (binding.pr_profile_read(ctx, 0)[0], binding.pr_profile_read(ctx, 1)[0]) == passes
+
+
+def test_fused_2d_cluster_rows_2048_whole_slices(lib):
+    """160 slices of 2048^2: a cluster's row range holds whole slices, whose
+    halo rows wrap around the periodic slice at both ends.  Four distinct
+    slice states are tiled over the batch; the first, two middle and the last
+    slices are checked against the oracle."""
+    import torch
+    from paper_1905_00473_gb300 import binding
+    N = 160
+    w = W.custom_case(2, 2048, N, 9, "f32", "inclusion")   # 10 levels: 8 + 2
+    ctx = P.make_ctx(w)
+    w4 = W.custom_case(2, 2048, 4, 9, "f32", "inclusion")
+    u4, v4 = W.slice_states(w4, seed=13)
+    u4d = torch.tensor(u4, dtype=torch.float32, device="cuda")
+    v4d = torch.tensor(v4, dtype=torch.float32, device="cuda")
+    reps = N // 4
+    ud = u4d.repeat(reps, 1, 1).contiguous()
+    vd = v4d.repeat(reps, 1, 1).contiguous()
+    uo = torch.full_like(ud, float("nan"))
+    vo = torch.full_like(vd, float("nan"))
+    binding.pr_fine_all_slices(ctx, ud, vd, uo, vo)
+    binding.pr_check(ctx)
+    for s in (0, 77, 82, N - 1):
+        ur, vr = P.oracle_slice(w, u4[s % 4], v4[s % 4])
+        ug = uo[s].double().cpu().numpy()
+        vg = vo[s].double().cpu().numpy()
+        e, l2 = P.slice_errors(w, ug, vg, ur, vr)
+        assert e <= P.tol_for(w), (s, e)
+        assert l2 <= P.tol_for(w), (s, l2)
 
 
 @pytest.mark.parametrize("cols", [2, 4])
