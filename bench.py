@@ -208,9 +208,12 @@ def dist_env():
 def workload_for(cfg: str, slices: int = 0) -> W.Workload:
     """The configuration's workload; slices > 0 keeps the grid, medium and
     time step but propagates only that many slices (small profiling runs)."""
-    if cfg not in ("2", "3"):
-        raise SystemExit("--config must be 2 or 3 (2D FP32 sweeps)")
-    w = W.CONFIGS[cfg]()
+    if cfg.startswith("4:"):   # one instance of the uneven batch, alone
+        w = W.config4_instance(int(cfg[2:]))
+    elif cfg in ("2", "3"):
+        w = W.CONFIGS[cfg]()
+    else:
+        raise SystemExit("--config must be 2, 3 or 4:<instance> for a sweep, or 4 for the batch")
     if slices and slices != w.n_slices:
         m_f = w.m_f
         w.t_final = w.t_final * slices / w.n_slices
@@ -600,7 +603,8 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", default="3")
+    ap.add_argument("--config", default="3",
+                    help="2, 3: the sweep workloads; 4: the uneven batch; 4:<i>: instance i of the batch alone")
     ap.add_argument("--block-depth", type=int, default=0, help="0 = library default")
     ap.add_argument("--columns", type=int, default=0, choices=[0, 2, 4],
                     help="fused-kernel columns per thread (0 = library default)")
