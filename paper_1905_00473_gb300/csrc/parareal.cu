@@ -260,6 +260,14 @@ __global__ void copy_block(const double* __restrict__ A, int64_t lda, double* __
         B[(int64_t)col * ldb + ro + row] = A[(int64_t)col * lda + row];
     }
 }
+// B(ro + i, j) = A(j, i) for i < rows, j < cols (A with leading dimension lda)
+__global__ void copy_block_t(const double* __restrict__ A, int64_t lda, double* __restrict__ B, int64_t ldb,
+                             int rows, int cols, int ro) {
+    for (int64_t idx = (int64_t)blockIdx.x * kT + threadIdx.x; idx < (int64_t)rows * cols; idx += (int64_t)gridDim.x * kT) {
+        const int col = (int)(idx / rows), row = (int)(idx - (int64_t)col * rows);
+        B[(int64_t)col * ldb + ro + row] = A[(int64_t)row * lda + col];
+    }
+}
 __global__ void add_diag(double* __restrict__ H, int64_t ld, const double* __restrict__ S, int s) {
     for (int i = blockIdx.x * kT + threadIdx.x; i < s; i += gridDim.x * kT) H[(int64_t)i * ld + i] += S[i];
 }
@@ -291,14 +299,18 @@ struct pr_driver {
     double* zero = nullptr;                         // device scalar
     cufftDoubleComplex* zc = nullptr;               // [max(d,2) * cpts]
     cufftDoubleComplex* zf = nullptr;               // [2 * pts]
-    // SVD state: X, Y [rows][cap], S [cap]
-    double* X = nullptr; double* Y = nullptr; double* S = nullptr;
-    int s = 0, cap = 0;
+    // SVD state of Alg. 1, kept factored: X = Xb WX, Y = Yb WY.  Xb, Yb
+    // [rows][bcap] hold every orthonormalised block Q_F, Q_G appended so far
+    // (hb columns); WX, WY [bcap][bcap] (hb x s in use) map them onto the s
+    // kept singular directions, so an update rotates only WX, WY.
+    double *Xb = nullptr, *Yb = nullptr, *WX = nullptr, *WY = nullptr, *WXn = nullptr, *WYn = nullptr;
+    double *Tb = nullptr, *vb = nullptr;   // [bcap][N] and [2 bcap] scratch
+    double* S = nullptr;                   // [bcap]
+    int s = 0, hb = 0, bcap = 0;
     // UpdateSVD scratch
     double *QF = nullptr, *QG = nullptr, *RF = nullptr, *RG = nullptr, *tau = nullptr;
     double *UF = nullptr, *VG = nullptr, *A1 = nullptr, *A2 = nullptr, *H = nullptr;
     double *Xh = nullptr, *YhT = nullptr, *sig = nullptr, *work = nullptr, *rwork = nullptr;
-    double *Xn = nullptr, *Yn = nullptr;
     double *F2 = nullptr, *G2 = nullptr;            // copies of F, G for the residual
     int* info = nullptr;
     int64_t work_len = 0;
@@ -323,9 +335,9 @@ void pr_driver_free(pr_ctx* ctx) {
     for (cudaEvent_t e : d->ev)
         if (e) cudaEventDestroy(e);
     void* bufs[] = {d->vF_u, d->vF_v, d->Uc_u, d->Uc_v, d->w_u, d->w_v, d->Fm, d->Gm, d->dvec, d->gvec,
-                    d->du, d->dut, d->zero, d->zc, d->zf, d->X, d->Y, d->S, d->QF, d->QG, d->RF, d->RG,
-                    d->tau, d->UF, d->VG, d->A1, d->A2, d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork,
-                    d->Xn, d->Yn, d->F2, d->G2, d->info};
+                    d->du, d->dut, d->zero, d->zc, d->zf, d->Xb, d->Yb, d->WX, d->WY, d->WXn, d->WYn,
+                    d->Tb, d->vb, d->S, d->QF, d->QG, d->RF, d->RG, d->tau, d->UF, d->VG, d->A1, d->A2,
+                    d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork, d->F2, d->G2, d->info};
     for (void* b : bufs) cudaFree(b);
     delete d;
     ctx->drv = nullptr;
@@ -513,27 +525,39 @@ pr_status coarse_of(pr_ctx* ctx, const void* u, const void* v, void* U, void* V,
 // ---------------------------------------------------------------- UpdateSVD (Alg. 1)
 pr_status ensure_capacity(pr_ctx* ctx, pr_driver* d, int need_s, int ncols, cudaStream_t st) {
     const int64_t rows = d->rows;
-    if (need_s > d->cap || need_s > d->hcap) {
+    const int need_b = d->hb + ncols;   // stored columns after this update
+    if (need_b > d->bcap || need_s > d->hcap) {
         cudaError_t e = cudaStreamSynchronize(st);   // buffers below are still in use by st
         if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "svd: synchronize");
     }
-    if (need_s > d->cap) {
-        int cap = std::max(need_s, d->cap * 2);
-        cap = (int)std::min<int64_t>(cap, rows + ncols);
-        double *X = nullptr, *Y = nullptr, *S = nullptr, *Xn = nullptr, *Yn = nullptr;
-        PR_TRY_ST(alloc(ctx, (void**)&X, (size_t)rows * cap * 8, "svd: alloc"));
-        PR_TRY_ST(alloc(ctx, (void**)&Y, (size_t)rows * cap * 8, "svd: alloc"));
-        PR_TRY_ST(alloc(ctx, (void**)&S, (size_t)cap * 8, "svd: alloc"));
-        PR_TRY_ST(alloc(ctx, (void**)&Xn, (size_t)rows * cap * 8, "svd: alloc"));
-        PR_TRY_ST(alloc(ctx, (void**)&Yn, (size_t)rows * cap * 8, "svd: alloc"));
+    if (need_b > d->bcap) {
+        const int bc = std::max(need_b, d->bcap * 2);
+        double *Xb = nullptr, *Yb = nullptr, *WX = nullptr, *WY = nullptr, *WXn = nullptr, *WYn = nullptr;
+        double *Tb = nullptr, *vb = nullptr, *S = nullptr;
+        PR_TRY_ST(alloc(ctx, (void**)&Xb, (size_t)rows * bc * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&Yb, (size_t)rows * bc * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&WX, (size_t)bc * bc * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&WY, (size_t)bc * bc * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&WXn, (size_t)bc * bc * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&WYn, (size_t)bc * bc * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&Tb, (size_t)bc * d->N * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&vb, (size_t)2 * bc * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&S, (size_t)bc * 8, "svd: alloc"));
         if (d->s > 0) {
-            cudaMemcpy(X, d->X, (size_t)rows * d->s * 8, cudaMemcpyDeviceToDevice);
-            cudaMemcpy(Y, d->Y, (size_t)rows * d->s * 8, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(Xb, d->Xb, (size_t)rows * d->hb * 8, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(Yb, d->Yb, (size_t)rows * d->hb * 8, cudaMemcpyDeviceToDevice);
+            // hb x s blocks, leading dimension bcap -> bc
+            cudaMemcpy2D(WX, (size_t)bc * 8, d->WX, (size_t)d->bcap * 8, (size_t)d->hb * 8, d->s,
+                         cudaMemcpyDeviceToDevice);
+            cudaMemcpy2D(WY, (size_t)bc * 8, d->WY, (size_t)d->bcap * 8, (size_t)d->hb * 8, d->s,
+                         cudaMemcpyDeviceToDevice);
             cudaMemcpy(S, d->S, (size_t)d->s * 8, cudaMemcpyDeviceToDevice);
         }
-        cudaFree(d->X); cudaFree(d->Y); cudaFree(d->S); cudaFree(d->Xn); cudaFree(d->Yn);
-        d->X = X; d->Y = Y; d->S = S; d->Xn = Xn; d->Yn = Yn;
-        d->cap = cap;
+        double** olds[] = {&d->Xb, &d->Yb, &d->WX, &d->WY, &d->WXn, &d->WYn, &d->Tb, &d->vb, &d->S};
+        for (double** o : olds) cudaFree(*o);
+        d->Xb = Xb; d->Yb = Yb; d->WX = WX; d->WY = WY; d->WXn = WXn; d->WYn = WYn;
+        d->Tb = Tb; d->vb = vb; d->S = S;
+        d->bcap = bc;
     }
     const int h = need_s;   // (s + ncols)
     if (h > d->hcap || !d->QF) {
@@ -611,19 +635,42 @@ int rank_cut_host(const std::vector<double>& sig, double tol) {
     return r;
 }
 
-// Alg. 1 with F, G (rows x nc, column-major, consumed).  Updates d->X,S,Y,s.
+// C (rows x nc) = B^T A with B = Bb W (Bb rows x hb, W hb x s, ld bcap): C is
+// s x nc, through T = Bb^T A (hb x nc)
+pr_status project_(pr_ctx* ctx, pr_driver* d, const double* Bb, const double* W, const double* A, int nc,
+                   double* C) {
+    const double one = 1.0, zero = 0.0;
+    const int64_t rows = d->rows;
+    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, d->hb, nc, (int)rows, &one, Bb, (int)rows, A, (int)rows, &zero, d->Tb, d->hb), "Bb^T A");
+    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, d->s, nc, d->hb, &one, W, d->bcap, d->Tb, d->hb, &zero, C, d->s), "W^T T");
+    return PR_OK;
+}
+// A -= (Bb W) C for C (s x nc), through T = W C (hb x nc)
+pr_status subtract_(pr_ctx* ctx, pr_driver* d, const double* Bb, const double* W, const double* C, int nc,
+                    double* A) {
+    const double one = 1.0, zero = 0.0, mone = -1.0;
+    const int64_t rows = d->rows;
+    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, d->hb, nc, d->s, &one, W, d->bcap, C, d->s, &zero, d->Tb, d->hb), "W C");
+    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, nc, d->hb, &mone, Bb, (int)rows, d->Tb, d->hb, &one, A, (int)rows), "A - Bb T");
+    return PR_OK;
+}
+
+// Alg. 1 with F, G (rows x nc, column-major, consumed).  Updates the factored
+// X, Y (X = Xb WX, Y = Yb WY), S and s: the new bases [X Q_F] X_h, [Y Q_G] Y_h
+// are [Xb Q_F] [WX 0; 0 I] X_h and the same for Y, so Q_F, Q_G are appended
+// to Xb, Yb and only the small WX, WY are rotated.
 pr_status update_svd(pr_ctx* ctx, pr_driver* d, double* F, double* G, int nc, cudaStream_t st) {
     const int64_t rows = d->rows;
     const int s = d->s;
-    const double one = 1.0, zero = 0.0, mone = -1.0;
+    const double one = 1.0, zero = 0.0;
     PR_TRY_ST(ensure_capacity(ctx, d, s + nc, nc, st));
     const int h = s + nc;
     if (s > 0) {
         // U_F = U^T F, V_G = V^T G, then F - U U_F, G - V V_G
-        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, s, nc, (int)rows, &one, d->X, (int)rows, F, (int)rows, &zero, d->UF, s), "UtF");
-        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, s, nc, (int)rows, &one, d->Y, (int)rows, G, (int)rows, &zero, d->VG, s), "VtG");
-        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, nc, s, &mone, d->X, (int)rows, d->UF, s, &one, F, (int)rows), "F-UUF");
-        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, nc, s, &mone, d->Y, (int)rows, d->VG, s, &one, G, (int)rows), "G-VVG");
+        PR_TRY_ST(project_(ctx, d, d->Xb, d->WX, F, nc, d->UF));
+        PR_TRY_ST(project_(ctx, d, d->Yb, d->WY, G, nc, d->VG));
+        PR_TRY_ST(subtract_(ctx, d, d->Xb, d->WX, d->UF, nc, F));
+        PR_TRY_ST(subtract_(ctx, d, d->Yb, d->WY, d->VG, nc, G));
     }
     cudaMemcpyAsync(d->QF, F, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(d->QG, G, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
@@ -644,19 +691,25 @@ pr_status update_svd(pr_ctx* ctx, pr_driver* d, double* F, double* G, int nc, cu
     const int r = rank_cut_host(sig, ctx->opts.tol);
     if (r == 0) {
         d->s = 0;
+        d->hb = 0;
         return PR_OK;
     }
-    // U~ = [U Q_F] X_h(:, 1:r), V~ = [V Q_G] Y_h(:, 1:r)   (Y_h = YhT^T)
+    // U~ = [U Q_F] X_h(:, 1:r), V~ = [V Q_G] Y_h(:, 1:r)   (Y_h = YhT^T):
+    // Xb <- [Xb Q_F], WX <- [WX X_h(1:s, 1:r); X_h(s+1:h, 1:r)], likewise Y
+    const int hb = d->hb, ld = d->bcap;
+    cudaMemcpyAsync(d->Xb + (int64_t)hb * rows, d->QF, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(d->Yb + (int64_t)hb * rows, d->QG, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
     if (s > 0) {
-        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, r, s, &one, d->X, (int)rows, d->Xh, h, &zero, d->Xn, (int)rows), "Xn");
-        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_T, (int)rows, r, s, &one, d->Y, (int)rows, d->YhT, h, &zero, d->Yn, (int)rows), "Yn");
+        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, hb, r, s, &one, d->WX, ld, d->Xh, h, &zero, d->WXn, ld), "WX Xh");
+        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_T, hb, r, s, &one, d->WY, ld, d->YhT, h, &zero, d->WYn, ld), "WY Yh");
     }
-    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, r, nc, &one, d->QF, (int)rows, d->Xh + s, h, s > 0 ? &one : &zero, d->Xn, (int)rows), "Xn+");
-    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_T, (int)rows, r, nc, &one, d->QG, (int)rows, d->YhT + (int64_t)s * h, h, s > 0 ? &one : &zero, d->Yn, (int)rows), "Yn+");
-    std::swap(d->X, d->Xn);
-    std::swap(d->Y, d->Yn);
+    copy_block<<<blocks_for((int64_t)nc * r), kT, 0, st>>>(d->Xh + s, h, d->WXn, ld, nc, r, hb);
+    copy_block_t<<<blocks_for((int64_t)nc * r), kT, 0, st>>>(d->YhT + (int64_t)s * h, h, d->WYn, ld, nc, r, hb);
+    std::swap(d->WX, d->WXn);
+    std::swap(d->WY, d->WYn);
     cudaMemcpyAsync(d->S, d->sig, (size_t)r * 8, cudaMemcpyDeviceToDevice, st);
     d->s = r;
+    d->hb = hb + nc;
     return PR_OK;
 }
 
@@ -667,23 +720,27 @@ pr_status apply_omega(pr_ctx* ctx, pr_driver* d, const double* g, double* out, c
         cudaMemsetAsync(out, 0, (size_t)d->rows * 8, st);
         return PR_OK;
     }
-    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_T, (int)d->rows, d->s, &one, d->Y, (int)d->rows, g, 1, &zero, d->rwork, 1), "Ytg");
-    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_N, (int)d->rows, d->s, &one, d->X, (int)d->rows, d->rwork, 1, &zero, out, 1), "Xt");
+    // X (Y^T g) = Xb (WX (WY^T (Yb^T g)))
+    double* t1 = d->vb;
+    double* t2 = d->vb + d->bcap;
+    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_T, (int)d->rows, d->hb, &one, d->Yb, (int)d->rows, g, 1, &zero, t1, 1), "Yb^T g");
+    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_T, d->hb, d->s, &one, d->WY, d->bcap, t1, 1, &zero, d->rwork, 1), "WY^T");
+    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_N, d->hb, d->s, &one, d->WX, d->bcap, d->rwork, 1, &zero, t2, 1), "WX");
+    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_N, (int)d->rows, d->hb, &one, d->Xb, (int)d->rows, t2, 1, &zero, out, 1), "Xb");
     return PR_OK;
 }
 
 // ||F - X Y^T G||_F / ||F||_F for the current data (F, G unmodified copies in Fm/Gm)
 pr_status residual_(pr_ctx* ctx, pr_driver* d, const double* F, const double* G, int nc, double* res,
                     cudaStream_t st) {
-    const double one = 1.0, zero = 0.0, mone = -1.0;
     const int64_t rows = d->rows;
     double nf = 0, nr = 0;
     PR_BLAS(ctx, cublasDnrm2(d->blas, (int)(rows * nc), F, 1, &nf), "nrm2");
     // QF (rows x nc) <- F - X (Y^T G): reuse QF/UF scratch (UF has >= s*nc)
     cudaMemcpyAsync(d->QF, F, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
     if (d->s > 0) {
-        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, d->s, nc, (int)rows, &one, d->Y, (int)rows, G, (int)rows, &zero, d->UF, d->s), "YtG");
-        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, nc, d->s, &mone, d->X, (int)rows, d->UF, d->s, &one, d->QF, (int)rows), "F-XYtG");
+        PR_TRY_ST(project_(ctx, d, d->Yb, d->WY, G, nc, d->UF));
+        PR_TRY_ST(subtract_(ctx, d, d->Xb, d->WX, d->UF, nc, d->QF));
     }
     PR_BLAS(ctx, cublasDnrm2(d->blas, (int)(rows * nc), d->QF, 1, &nr), "nrm2");
     *res = nf > 0 ? nr / nf : 0.0;
@@ -742,7 +799,10 @@ extern "C" pr_status pr_procrustes_apply(pr_ctx* ctx, const double* g, double* o
 
 extern "C" pr_status pr_procrustes_reset(pr_ctx* ctx) {
     if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_procrustes_reset: ctx is NULL");
-    if (ctx->drv) ctx->drv->s = 0;
+    if (ctx->drv) {
+        ctx->drv->s = 0;
+        ctx->drv->hb = 0;
+    }
     return PR_OK;
 }
 
@@ -759,6 +819,7 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
     pr_driver* d = nullptr;
     PR_TRY_ST(driver(ctx, st, &d));
     d->s = 0;   // a new run starts with an empty correlation matrix (Alg. 3)
+    d->hb = 0;
     for (int i = 0; i < 4; ++i) {
         d->phase_ms[i] = 0.0;
         if (!d->ev[i]) PR_CUDA_TRY(ctx, cudaEventCreate(&d->ev[i]));
