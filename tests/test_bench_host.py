@@ -1,0 +1,46 @@
+"""Host-side logic of bench.py (no GPU): workload selection, the kernel-source
+hash that decides whether the committed ncu traffic figure still applies, and
+the lookup of that figure."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def test_workload_selection():
+    w3 = bench.workload_for("3")
+    assert (w3.n_fine, w3.n_slices, w3.m_f) == (1024, 64, 384)
+    w2 = bench.workload_for("2", slices=4)
+    assert (w2.n_fine, w2.n_slices, w2.m_f) == (512, 4, 192)   # fewer slices, same step
+    wi = bench.workload_for("4:3", slices=8)
+    assert (wi.n_fine, wi.n_slices) == (2048, 8)
+    assert wi.m_f == bench.workload_for("4:3").m_f
+    for bad in ("1", "5", "4:x", "7"):
+        with pytest.raises((SystemExit, ValueError)):
+            bench.workload_for(bad)
+
+
+def test_kernel_hash_ignores_comments_but_not_code():
+    src = {rel: open(os.path.join(bench.ROOT, rel)).read() for rel in bench.KERNEL_SOURCES}
+    base = bench.kernel_source_hash(lambda rel: src[rel])
+    assert base == bench.kernel_source_hash()
+    first = bench.KERNEL_SOURCES[0]
+    commented = dict(src)
+    commented[first] = "// a comment\n/* a block\n comment */\n" + src[first].replace("\n", "  \n", 3)
+    assert bench.kernel_source_hash(lambda rel: commented[rel]) == base
+    edited = dict(src)
+    edited[first] = src[first] + "\nstatic int an_edit = 1;\n"
+    assert bench.kernel_source_hash(lambda rel: edited[rel]) != base
+
+
+def test_traffic_figure_only_for_the_profiled_source(monkeypatch):
+    with open(os.path.join(bench.ROOT, "profiles", "fine_tb2d_traffic.json")) as f:
+        d = json.load(f)
+    key, val = next(iter(d["per_launch_bytes"].items()))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda read=None: d["source_hash"])
+    assert bench.ncu_traffic(key) == val
+    assert bench.ncu_traffic("no-such-workload") is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda read=None: "0" * 16)
+    assert bench.ncu_traffic(key) is None
