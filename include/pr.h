@@ -182,6 +182,9 @@ pr_status pr_iterate_phases(const pr_ctx* ctx, double* ms);
  *  Fcols, Gcols  DEVICE double [ncols][(d+1) n_c^d], one column per slice
  *                (eq. matrixF / matrixG: [nabla_h w ; c^-1 w_t], x-derivative
  *                block first), 1 <= ncols <= N.
+ * X and Y are held factored (X = X_b W_X): every update appends its ncols
+ * orthonormalised columns to X_b, Y_b in context memory (2 (d+1) n_c^d
+ * doubles per column) until pr_procrustes_reset or the next pr_iterate.
  * Synchronises the stream. */
 pr_status pr_procrustes_correct(pr_ctx* ctx, const double* Fcols, const double* Gcols, int ncols,
                                 void* stream);
