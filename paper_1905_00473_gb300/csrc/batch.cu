@@ -28,11 +28,6 @@ namespace {
 
 constexpr int kStreams = 8;
 
-pr_status bfail(pr_batch* b, pr_status s, const std::string& m) {
-    if (b) b->err = m;
-    return pr_fail(nullptr, s, m);
-}
-
 void destroy(pr_batch* b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
