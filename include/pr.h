@@ -159,6 +159,8 @@ pr_status pr_coarse_sweep(pr_ctx* ctx, const void* u, const void* v, void* U_out
  * the dense factorisations).  The correction of a slice is applied to the
  * difference Lambda w - Lambda U_n with zero mode sum w - sum U_n, which by
  * linearity equals Alg. 3's two applications.  Synchronises the stream.
+ * Reads the device-side error flags of the fine and coarse sweeps after every
+ * iteration: PR_ETIMEOUT (flags cleared) if a bounded wait gave up.
  * Requires grad_order 2, 4, 6 or 8.  Returns PR_EUNSTABLE if the energy of
  * the state at T stops being finite (the stability the method is built to
  * keep, Sec. 5). */
@@ -225,12 +227,16 @@ typedef struct pr_batch pr_batch;
  * biggest first, spread over 8 library-owned streams between a fork and a
  * join.  Runs (and synchronises) the timing sweeps; the bound arrays must
  * stay valid until pr_batch_destroy.  The contexts must not be used
- * concurrently with a launch of the batch. */
+ * concurrently with a launch of the batch.  PR_EINVAL if a context appears
+ * twice or an output array overlaps an array of another instance (inputs may
+ * be shared between instances; in == out within one instance is allowed). */
 pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void* const* u_in,
                           const void* const* v_in, void* const* u_out, void* const* v_out,
                           int autotune, void* stream, pr_batch** out);
 
-/* pr_batch_launch -- replay the captured graph on `stream` (asynchronous). */
+/* pr_batch_launch -- replay the captured graph on `stream` (asynchronous).
+ * Device-side wait time-outs are reported by pr_check on each instance's
+ * context, after the launch has completed. */
 pr_status pr_batch_launch(pr_batch* b, void* stream);
 
 /* pr_batch_info -- chosen block depth, fused-kernel columns per thread (0 =

@@ -224,19 +224,28 @@ def pr_profile_read(ctx: Context, kind: int) -> tuple[int, float]:
 def pr_fine_all_slices_noalloc(c, dt_f: float, m_f: int, u_in, v_in, u_out, v_out,
                                stream=None) -> None:
     """Context-free F over all slices with the library's fixed device scratch
-    (no device allocation); FP32 tensors, shapes [N, n, ..., n] with c [n, ..., n]."""
+    (no device allocation); FP32 tensors, shapes [N, n, ..., n] with c [n, ..., n].
+    Shapes are checked first (ValueError), then dtype, device and layout
+    (TypeError), all before anything is launched."""
     import torch
     for name, t in (("c", c), ("u_in", u_in), ("v_in", v_in), ("u_out", u_out), ("v_out", v_out)):
-        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 \
-                or not t.is_contiguous():
-            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor")
     dim = c.dim()
+    if dim not in (1, 2, 3):
+        raise ValueError("c must have 1, 2 or 3 axes")
     n = int(c.shape[0])
+    if any(int(s) != n for s in c.shape):
+        # the C entry point takes one n for every axis (n^dim points per slice)
+        raise ValueError(f"c must have the same number of points on every axis, got {tuple(c.shape)}")
     if u_in.dim() != dim + 1 or tuple(u_in.shape[1:]) != tuple(c.shape):
         raise ValueError("u_in must be [N, *c.shape]")
     for t in (v_in, u_out, v_out):
         if t.shape != u_in.shape:
             raise ValueError("u_in, v_in, u_out, v_out must have the same shape")
+    for name, t in (("c", c), ("u_in", u_in), ("v_in", v_in), ("u_out", u_out), ("v_out", v_out)):
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
     msg = ctypes.create_string_buffer(512)
     st = load().pr_fine_all_slices_noalloc(
         dim, n, int(u_in.shape[0]), ctypes.c_void_p(c.data_ptr()), dt_f, m_f,

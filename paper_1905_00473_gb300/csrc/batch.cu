@@ -87,6 +87,38 @@ extern "C" pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void*
         b->cols.push_back(ctxs[i]->tb_cols);
         b->ms.push_back(0.0);
     }
+    // instances run concurrently on different streams and the autotuner
+    // writes every output while timing: a context used twice would race on its
+    // scratch, and an output overlapping another instance's arrays would
+    // clobber that instance's data
+    {
+        struct Span { uintptr_t lo, hi; int inst; bool out; };
+        std::vector<Span> spans;
+        for (int i = 0; i < count; ++i) {
+            for (int j = 0; j < i; ++j)
+                if (b->ctx[j] == b->ctx[i]) {
+                    destroy(b);
+                    return pr_fail(nullptr, PR_EINVAL, "pr_batch_create: a context appears twice");
+                }
+            const uintptr_t len = (uintptr_t)b->ctx[i]->N * (uintptr_t)b->ctx[i]->pts *
+                                  (b->ctx[i]->dtype == PR_F32 ? 4u : 8u);
+            spans.push_back({(uintptr_t)b->ui[i], (uintptr_t)b->ui[i] + len, i, false});
+            spans.push_back({(uintptr_t)b->vi[i], (uintptr_t)b->vi[i] + len, i, false});
+            spans.push_back({(uintptr_t)b->uo[i], (uintptr_t)b->uo[i] + len, i, true});
+            spans.push_back({(uintptr_t)b->vo[i], (uintptr_t)b->vo[i] + len, i, true});
+        }
+        for (size_t a = 0; a < spans.size(); ++a)
+            for (size_t c = 0; c < a; ++c) {
+                const Span& x = spans[a];
+                const Span& y = spans[c];
+                if (x.inst == y.inst || !(x.out || y.out)) continue;
+                if (x.lo < y.hi && y.lo < x.hi) {
+                    destroy(b);
+                    return pr_fail(nullptr, PR_EINVAL,
+                                   "pr_batch_create: an output array overlaps another instance's array");
+                }
+            }
+    }
     // autotuner: the fastest instantiated (depth, columns) per instance, timed once
     if (autotune) {
         const int cands[5][2] = {{8, 4}, {8, 2}, {4, 4}, {4, 2}, {1, 0}};

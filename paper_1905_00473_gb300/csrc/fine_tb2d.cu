@@ -696,9 +696,14 @@ __global__ void __launch_bounds__(NT, 1) fine_tb2d_kernel(const Tb2dParams p) {
         pos = next;
     }
     if (aborted && t == 0) {
-        // let copies still in flight land before the CTA's shared memory is released
-        for (uint32_t q = consumed; q < issued_end; ++q)
+        // let copies still in flight land before the CTA's shared memory is
+        // released.  Under the time-out test hook every issued slot expects
+        // tx_extra bytes that no copy brings: settle them first, so that each
+        // wait ends exactly when the slot's real copies have landed
+        for (uint32_t q = consumed; q < issued_end; ++q) {
+            if (p.tx_extra) mbar_complete_tx(S::bar(sm, q % kU), p.tx_extra);
             (void)mbar_wait_bounded(S::bar(sm, q % kU), (q / kU) & 1u, p.wait_ns / 10);
+        }
     }
     if constexpr (CL > 1) {
         // The partner's pushes of its last step (and, after an abort, of the

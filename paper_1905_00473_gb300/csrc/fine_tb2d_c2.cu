@@ -359,9 +359,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) fine_tb2d_c2_kernel(const Tb2dPa
         pos = next;
     }
     if (aborted && t == 0) {
-        // let copies still in flight land before the CTA's shared memory is released
-        for (uint32_t q = consumed; q < issued_end; ++q)
+        // let copies still in flight land before the CTA's shared memory is
+        // released (test hook: settle the tx_extra bytes no copy brings first)
+        for (uint32_t q = consumed; q < issued_end; ++q) {
+            if (p.tx_extra) mbar_complete_tx(&sh.bars[q % kU], p.tx_extra);
             (void)mbar_wait_bounded(&sh.bars[q % kU], (q / kU) & 1u, p.wait_ns / 10);
+        }
     }
 }
 

@@ -912,6 +912,11 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
         // stability guard: the energy of the state at T must stay finite
         double e_T = 0.0;
         PR_TRY_ST(pr_launch_energy(ctx, fu(N), fv(N), 1, &e_T, st));
+        // a fused pass whose bounded wait gave up leaves its slices unpropagated
+        // (later passes of that context skip their work): report it, do not
+        // return this iteration's states as if they were valid
+        PR_TRY_ST(pr_take_flag(ctx, ctx, st, "pr_iterate (fine sweep)"));
+        if (ctx->coarse) PR_TRY_ST(pr_take_flag(ctx->coarse, ctx, st, "pr_iterate (coarse sweep)"));
         if (!isfinite(e_T)) {
             char buf[96];
             snprintf(buf, sizeof buf, "pr_iterate: energy at T is not finite after iteration %d", k);

@@ -413,20 +413,27 @@ extern "C" pr_status pr_debug_stall_waits(pr_ctx* ctx, int enable) {
     return PR_OK;
 }
 
+pr_status pr_take_flag(pr_ctx* ctx, pr_ctx* report, cudaStream_t st, const char* where) {
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, ctx->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return pr_cuda_fail(report, e, where);
+    if (flag) {
+        e = cudaMemsetAsync(ctx->dev_flag, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return pr_cuda_fail(report, e, where);
+        char buf[160];
+        snprintf(buf, sizeof buf, "%s: a device-side bounded wait gave up (code %d)", where, flag);
+        return pr_fail(report, PR_ETIMEOUT, buf);
+    }
+    return PR_OK;
+}
+
 extern "C" pr_status pr_check(pr_ctx* ctx, void* stream) {
     if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_check: ctx is NULL");
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "pr_check: stream synchronize");
-    int flag = 0;
-    e = cudaMemcpy(&flag, ctx->dev_flag, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "pr_check: read flag");
-    if (flag) {
-        cudaMemset(ctx->dev_flag, 0, sizeof(int));
-        char buf[128];
-        snprintf(buf, sizeof buf, "a device-side bounded wait gave up (code %d)", flag);
-        return pr_fail(ctx, PR_ETIMEOUT, buf);
-    }
-    return PR_OK;
+    return pr_take_flag(ctx, ctx, (cudaStream_t)stream, "pr_check");
 }
 
 extern "C" pr_status pr_energy(pr_ctx* ctx, const void* u, const void* v, int n_begin, int n_end,

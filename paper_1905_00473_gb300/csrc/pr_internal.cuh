@@ -59,6 +59,10 @@ void pr_driver_free(pr_ctx* ctx);
 // ---- status helpers --------------------------------------------------------
 pr_status pr_fail(pr_ctx* ctx, pr_status st, const std::string& msg);
 pr_status pr_cuda_fail(pr_ctx* ctx, cudaError_t e, const char* what);
+// Read (after the work queued on st) and clear ctx's device-side error flag;
+// PR_ETIMEOUT with the message recorded on `report` if a bounded wait gave up.
+// Synchronises st.
+pr_status pr_take_flag(pr_ctx* ctx, pr_ctx* report, cudaStream_t st, const char* where);
 
 #define PR_CUDA_TRY(ctx, call)                                   \
     do {                                                         \

@@ -17,6 +17,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+// complete `bytes` transaction bytes of the current phase without a copy
+// (no arrival): settles bytes that an expect_tx announced but no copy brings
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
 // a plain arrival (no transaction bytes): completes the phase of a slot that
 // receives no copy, so every slot completes one phase per ring lap
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {

@@ -49,3 +49,23 @@ def test_null_arguments_are_rejected_without_a_device(libpath):
     assert b"NULL" in lib.pr_last_error(None)
     assert lib.pr_fine_all_slices(None, None, None, None, None, 0, 1, None) == 1
     lib.pr_destroy(None)
+
+
+def test_noalloc_binding_rejects_unequal_axes_before_any_launch():
+    # the allocation-free entry point takes one n for all axes; a 256 x 128
+    # field would make it read and write n^2 points per slice past the end of
+    # every buffer, so the binding refuses it before the library is called
+    import torch
+    c = torch.ones((256, 128))
+    u = torch.zeros((2, 256, 128))
+    with pytest.raises(ValueError, match="every axis"):
+        binding.pr_fine_all_slices_noalloc(c, 1e-3, 4, u, u, u.clone(), u.clone())
+    c3 = torch.ones((16, 16, 8))
+    u3 = torch.zeros((1, 16, 16, 8))
+    with pytest.raises(ValueError, match="every axis"):
+        binding.pr_fine_all_slices_noalloc(c3, 1e-3, 4, u3, u3, u3.clone(), u3.clone())
+    # equal axes but mismatched slice shapes are refused too
+    with pytest.raises(ValueError):
+        binding.pr_fine_all_slices_noalloc(torch.ones((8, 8)), 1e-3, 4, torch.zeros((2, 8, 4)),
+                                           torch.zeros((2, 8, 4)), torch.zeros((2, 8, 4)),
+                                           torch.zeros((2, 8, 4)))

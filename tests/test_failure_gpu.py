@@ -50,3 +50,27 @@ def test_non_finite_state_is_reported_unstable(lib):
     with pytest.raises(binding.PrError) as ei:
         binding.pr_iterate(ctx, u0, torch.zeros_like(u0), 2, binding.PR_CORR_PLAIN, us, vs)
     assert ei.value.status == 5
+
+
+def test_bounded_wait_inside_iterate_is_reported(lib):
+    """pr_iterate reads the fine and coarse contexts' device flags after each
+    iteration: a fused pass that gave up waiting makes it return PR_ETIMEOUT
+    instead of states that were never propagated."""
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = W.custom_case(2, 256, 2, 8, "f32", "smooth")
+    c = torch.tensor(w.c, dtype=torch.float32, device="cuda")
+    ctx = binding.pr_create(2, 256, 4, c, w.dt_f, w.dt_c, 2, w.t_final)
+    assert binding.pr_info(ctx)["block_depth"] == 8
+    u0 = torch.tensor(W.periodic_gaussian(2, 256, (0.5, 0.5), 0.1), dtype=torch.float32,
+                      device="cuda")
+    us = torch.zeros((3, 256, 256), dtype=torch.float32, device="cuda")
+    vs = torch.zeros_like(us)
+    binding.pr_debug_stall_waits(ctx, True)
+    with pytest.raises(binding.PrError) as ei:
+        binding.pr_iterate(ctx, u0, torch.zeros_like(u0), 1, binding.PR_CORR_PLAIN, us, vs)
+    assert ei.value.status == 4 and "bounded wait" in str(ei.value)
+    binding.pr_debug_stall_waits(ctx, False)
+    binding.pr_check(ctx)                                  # the flag was cleared by pr_iterate
+    out = binding.pr_iterate(ctx, u0, torch.zeros_like(u0), 1, binding.PR_CORR_PLAIN, us, vs)
+    assert out["k_done"] == 1 and torch.isfinite(us).all()

@@ -232,3 +232,52 @@ def test_phase_timers_cover_the_call(lib):
     assert all(v >= 0.0 for v in ph.values()), ph
     assert ph["parallel_ms"] > 0 and ph["corrector_ms"] > 0 and ph["serial_update_ms"] > 0, ph
     assert sum(ph.values()) <= wall_ms * 1.05 + 0.5, (ph, wall_ms)
+
+
+def _run_workload(w, corrector, K, tol):
+    """pr_iterate on a named workload (its own u0, p0, ratio, grad order)."""
+    import torch
+    from paper_1905_00473_gb300 import binding
+    ctx = _ctx(w, w.ratio, w.grad_order, tol)
+    dt = torch.float32 if w.dtype == "f32" else torch.float64
+    u0 = torch.tensor(w.u0, dtype=dt, device="cuda")
+    p0 = torch.tensor(w.p0, dtype=dt, device="cuda")
+    us = torch.zeros((w.n_slices + 1,) + w.shape, dtype=dt, device="cuda")
+    vs = torch.zeros_like(us)
+    out = binding.pr_iterate(ctx, u0, p0, K, CORR[corrector], us, vs)
+    return us.double().cpu().numpy(), vs.double().cpu().numpy(), out
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+def test_config1_iterations_match_oracle(lib, K):
+    """The 1D FP64 workload in full (n = 128 / 32, N = 8, Procrustes, tol 1e-13,
+    K up to N = 8): every state u^{K+1}_n of the GPU driver equals the oracle's
+    to ~1e-9 relative in the energy norm, and the ranks agree."""
+    w = W.config1()
+    us, vs, out = _run_workload(w, "procrustes", K, 1e-13)
+    recs = parareal.iterate(_problem(w, "procrustes", tol=1e-13), w.u0, w.p0, K)
+    assert out["rank"] == [r.rank for r in recs]
+    final = recs[-1].states
+    for nn in range(1, w.n_slices + 1):
+        e = energy.relative_energy_error(us[nn], vs[nn], final[nn][0], final[nn][1], w.c, w.dx_f)
+        assert e <= 1e-9, (K, nn, e)
+
+
+@pytest.mark.slow
+def test_config2_iterations_match_oracle_fp32(lib):
+    """The smooth 2D FP32 workload at full size (512^2 / 128^2, N = 32, m_F =
+    192, Procrustes with the rank tolerance of its time-to-1e-4 run, 1e-7),
+    K = 2 iterations against the FP64 oracle on the same FP32-rounded inputs:
+    relative energy-norm error of every state <= 1e-4 (the FP32 parareal
+    bound).  The oracle takes about a minute here."""
+    w = W.config2()
+    K, tol = 2, 1e-7
+    us, vs, out = _run_workload(w, "procrustes", K, tol)
+    recs = parareal.iterate(_problem(w, "procrustes", tol=tol), w.u0, w.p0, K)
+    final = recs[-1].states
+    worst = 0.0
+    for nn in range(1, w.n_slices + 1):
+        e = energy.relative_energy_error(us[nn], vs[nn], final[nn][0], final[nn][1], w.c, w.dx_f)
+        worst = max(worst, e)
+    assert worst <= 1e-4, worst
+    assert out["rank"] == [r.rank for r in recs]

@@ -36,8 +36,14 @@ def test_noalloc_matches_context_path_twice(lib, dim, n, N, m_f):
         binding.pr_fine_all_slices(ctx, ud, vd, ur, vr)
         un = torch.full_like(ud, float("nan"))
         vn = torch.full_like(vd, float("nan"))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         binding.pr_fine_all_slices_noalloc(c, w.dt_f, w.m_f, ud, vd, un, vn)
         torch.cuda.synchronize()
+        if call == 1:
+            # the first call may load the kernels' code; the second, with the
+            # same kernels, must leave the device's free memory unchanged
+            assert torch.cuda.mem_get_info()[0] == free0
         a = [x.double().cpu().numpy() for x in (un, vn, ur, vr)]
         assert np.all(np.isfinite(a[0])) and np.all(np.isfinite(a[1]))
         err = _energy_err(w, *a)
