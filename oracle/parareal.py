@@ -94,6 +94,8 @@ class IterationRecord:
     rank: int                     # retained singular values s
     residual: Optional[float]     # ||F - Omega G||_F / ||F||_F of this iteration's data
     states: list                  # u^{k+1}_n, n = 0..N
+    X: Optional[np.ndarray] = None   # Omega^k = X Y^T used in this iteration's serial update
+    Y: Optional[np.ndarray] = None
 
 
 def iterate(P: Problem, u0: np.ndarray, p0: np.ndarray, K: int):
@@ -132,7 +134,7 @@ def iterate(P: Problem, u0: np.ndarray, p0: np.ndarray, K: int):
             cu, cut = I(P, du, dut)
             new.append((v[n - 1][0] + cu, v[n - 1][1] + cut))
         u = new
-        records.append(IterationRecord(k, 0 if S is None else int(S.size), residual, u))
+        records.append(IterationRecord(k, 0 if S is None else int(S.size), residual, u, X, Y))
     return records
 
 

@@ -146,3 +146,51 @@ def test_serial_update_pin_catches_a_misapplied_corrector(rotating_pair, monkeyp
         P.corrector = "omega1"
     err, _ = _max_error_after_one_iteration(P, u0, p0)
     assert err > 1e-2, (mutant, err)
+
+
+# ---- Sec. 6.2: the phase correction keeps long-time iterations stable ----
+
+def _sec62_errors(corrector: str, K: int) -> list:
+    """Relative energy error at T after k = 1..K iterations for the Sec. 6.2
+    study at T = 50: c = 1, one grid, Dx = 0.01, Dt_com = 0.05, Dt/Dx = 0.5,
+    Dt/dt = 20, 2nd-order nabla_h, tol 1e-14, u(x,0) = cos(10 pi x)
+    exp(-100 x^2) on [-0.5, 0.5), u_t(x,0) = 0 (the Sec. 6 initial data)."""
+    import math
+    n = 100
+    x = np.arange(n) / n - 0.5
+    u0 = np.cos(10 * math.pi * x) * np.exp(-100 * x ** 2)
+    P = parareal.Problem(c_fine=np.ones(n), ratio=1, n_slices=1000, dt_com=0.05, m_f=200, m_c=10,
+                         grad_order=2, tol=1e-14, corrector=corrector)
+    ref = parareal.serial_fine(P, u0, np.zeros(n))
+    return [parareal.relative_errors(P, r.states[-1], ref[-1])[0]
+            for r in parareal.iterate(P, u0, np.zeros(n), K)]
+
+
+def _sec62_errors_swapped(K: int) -> list:
+    """The same study with a planted mistake: Omega applied as Y X^T."""
+    procrustes.apply_corrector = _omega_apply_swapped
+    return _sec62_errors("procrustes", K)
+
+
+@pytest.mark.slow
+def test_phase_correction_stabilises_long_time_iterations():
+    """Sec. 6.2: for long terminal times the Omega = 1 coupling (Lambda^dagger
+    Lambda damping alone) goes unstable, while the Procrustes corrector
+    Omega^k_* stays stable.  At T = 50 (N = 1000 slices) the oracle's Omega = 1
+    error turns upward after ~10 iterations and passes 10x the initial error
+    by k = 14, while the Procrustes error decreases at every iteration.  With
+    X and Y swapped in the serial update (a planted mistake, in a separate
+    process) the error grows instead."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    K = 14
+    with cf.ProcessPoolExecutor(3, mp_context=mp.get_context("spawn")) as ex:
+        fo = ex.submit(_sec62_errors, "omega1", K)
+        fp = ex.submit(_sec62_errors, "procrustes", K)
+        fs = ex.submit(_sec62_errors_swapped, K)
+        e1, ep, es = fo.result(), fp.result(), fs.result()
+    assert max(e1) > 10 * e1[0], e1
+    assert e1[-1] > e1[9] * 5, e1
+    assert all(b < a for a, b in zip(ep, ep[1:])), ep
+    assert ep[-1] < 0.5 * ep[0], ep
+    assert es[-1] > 2 * es[0], es
