@@ -212,6 +212,35 @@ pr_status pr_procrustes_reset(pr_ctx* ctx);
 pr_status pr_adjoint(pr_ctx* ctx, const void* u0, const void* p0, const void* gu_T,
                      const void* gv_T, void* gc, void* gu0, void* gp0, void* stream);
 
+/* ---- products of the snapshot store on the tensor cores ------------------
+ * The tall-skinny products of UpdateSVD (Alg. 1): the projections of new
+ * data onto the kept bases, U_F = U^T F, V_G = V^T G, and the deflations
+ * F - U U_F, G - V V_G.  They run on the tcgen05 tensor cores: operands are
+ * FP64 in device memory, split while staged into shared memory into two
+ * TF32 halves (x = hi + lo), and each product is formed as hi*hi + hi*lo +
+ * lo*hi with FP32 accumulation ("3xTF32": about 2^-21 relative error per
+ * product, FP32-level accuracy).  pr_iterate uses them in FP32 contexts
+ * (FP64 contexts keep FP64 DGEMM).  The context supplies the device error
+ * flag of the bounded waits (reported by pr_check) and error messages; its
+ * grid is not used.  Arrays are DEVICE double, column-major, 8-byte aligned;
+ * asynchronous on `stream`.  PR_EINVAL for negative sizes, leading
+ * dimensions below the matrix height or NULL arrays, before any launch. */
+
+/* pr_snapshot_project -- C = A^T B.
+ *  A  K x M (lda >= K), B  K x N (ldb >= K), C  M x N (ldc >= M), overwritten.
+ * K is the long (snapshot-row) dimension; any M, N >= 0.  C must not overlap
+ * A or B. */
+pr_status pr_snapshot_project(pr_ctx* ctx, const double* A, int64_t lda, const double* B, int64_t ldb,
+                              int64_t K, int64_t M, int N, double* C, int64_t ldc, void* stream);
+
+/* pr_snapshot_deflate -- O = F - A T.
+ *  A  M x K (lda >= M), T  K x N (ldt >= K), F and O  M x N (ldf, ldo >= M).
+ * M is the long (snapshot-row) dimension.  O == F (same leading dimension)
+ * is allowed; any other overlap of O with F, A or T is rejected. */
+pr_status pr_snapshot_deflate(pr_ctx* ctx, const double* A, int64_t lda, const double* T, int64_t ldt,
+                              const double* F, int64_t ldf, int64_t M, int64_t K, int N, double* O,
+                              int64_t ldo, void* stream);
+
 /* ---- batches of independent instances of uneven sizes ------------------- */
 typedef struct pr_batch pr_batch;
 

@@ -76,6 +76,12 @@ _SIGNATURES = {
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double)]),
+    "pr_snapshot_project": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64,
+                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _P,
+                                           ctypes.c_int64, _P]),
+    "pr_snapshot_deflate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P,
+                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_int, _P, ctypes.c_int64, _P]),
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -374,3 +380,39 @@ def pr_set_fused_columns(ctx: Context, columns: int) -> None:
 
 def pr_debug_stall_waits(ctx: Context, enable: bool) -> None:
     _check(load().pr_debug_stall_waits(ctx.handle, 1 if enable else 0), ctx.handle)
+
+
+def _f64_matrix(name: str, t, rows: int, cols: int):
+    """(pointer, leading dimension) of a column-major FP64 CUDA matrix given as
+    a torch tensor of shape (cols, rows) (each column contiguous)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if t.dim() != 2 or t.shape[0] != cols or t.shape[1] != rows or t.stride(1) != 1:
+        raise ValueError(f"{name} must have shape ({cols}, {rows}) with unit stride in rows")
+    return ctypes.c_void_p(t.data_ptr()), max(int(t.stride(0)), rows, 1)
+
+
+def pr_snapshot_project(ctx: Context, A, B, C, stream=None) -> None:
+    """C = A^T B on the tensor cores (3xTF32).  Column-major matrices are
+    passed as tensors of shape (columns, rows): A (M, K), B (N, K), C (N, M)."""
+    M, K = int(A.shape[0]), int(A.shape[1])
+    N = int(B.shape[0])
+    pa, lda = _f64_matrix("A", A, K, M)
+    pb, ldb = _f64_matrix("B", B, K, N)
+    pc, ldc = _f64_matrix("C", C, M, N)
+    _check(load().pr_snapshot_project(ctx.handle, pa, lda, pb, ldb, K, M, N, pc, ldc,
+                                      ctypes.c_void_p(_stream_ptr(stream))), ctx.handle)
+
+
+def pr_snapshot_deflate(ctx: Context, A, T, F, O, stream=None) -> None:
+    """O = F - A T on the tensor cores (3xTF32).  Shapes (columns, rows):
+    A (K, M), T (N, K), F and O (N, M)."""
+    K, M = int(A.shape[0]), int(A.shape[1])
+    N = int(F.shape[0])
+    pa, lda = _f64_matrix("A", A, M, K)
+    pt, ldt = _f64_matrix("T", T, K, N)
+    pf, ldf = _f64_matrix("F", F, M, N)
+    po, ldo = _f64_matrix("O", O, M, N)
+    _check(load().pr_snapshot_deflate(ctx.handle, pa, lda, pt, ldt, pf, ldf, M, K, N, po, ldo,
+                                      ctypes.c_void_p(_stream_ptr(stream))), ctx.handle)

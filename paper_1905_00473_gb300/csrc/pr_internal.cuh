@@ -32,6 +32,8 @@ struct pr_ctx {
     void* adj_ws = nullptr;           // pr_adjoint workspace (adjoint.cu), lazily created
     int debug_stall = 0;              // pr_debug_stall_waits (tests of the time-out path)
     size_t adj_bytes = 0;
+    void* sadj_ws = nullptr;          // one-slice adjoint workspace (adjoint.cu), lazily created
+    size_t sadj_bytes = 0;
     // ping-pong state between passes, [N][pts] each: u, v (dtype), r (the
     // residual: resid_bytes per point, 2 where a fused 2D sweep may run)
     void* su[2] = {nullptr, nullptr};
@@ -55,6 +57,22 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
                        double dt_c, int m_c, const pr_options& o, const std::vector<double>& c,
                        pr_ctx** out);
 void pr_driver_free(pr_ctx* ctx);
+
+// ---- adjoint of one slice (adjoint.cu) ---------------------------------------
+// Reverse of the m_f + 1 levels of one slice of context c (fine or coarse)
+// started from (u_in, v_in): (lu, lv) hold the adjoints of the slice's end
+// state on entry and of its start state on return (dtype, [pts]); dL/dkappa
+// is added to gk (FP64, [pts]).
+pr_status pr_slice_adjoint(pr_ctx* c, const void* u_in, const void* v_in, void* lu, void* lv, double* gk,
+                           cudaStream_t st);
+
+// ---- snapshot products on the tensor cores (gram_tc.cu, 3xTF32) -------------
+// C (M x N, ldc) = A^T B, A (K x M, lda), B (K x N, ldb); C is overwritten.
+pr_status tc_gram_launch(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t K, int64_t M, int N,
+                         double* C, int64_t ldc, int* flag, cudaStream_t st);
+// O (M x N, ldo) = F - A T, A (M x K, lda), T (K x N, ldt); O may equal F.
+pr_status tc_update_launch(const double* A, int64_t lda, const double* T, int64_t ldt, const double* F, int64_t ldf,
+                           int64_t M, int64_t K, int N, double* O, int64_t ldo, int* flag, cudaStream_t st);
 
 // ---- status helpers --------------------------------------------------------
 pr_status pr_fail(pr_ctx* ctx, pr_status st, const std::string& msg);

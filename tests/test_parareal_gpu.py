@@ -281,3 +281,29 @@ def test_config2_iterations_match_oracle_fp32(lib):
         worst = max(worst, e)
     assert worst <= 1e-4, worst
     assert out["rank"] == [r.rank for r in recs]
+
+
+def test_update_svd_fp32_context_matches_oracle(lib):
+    """UpdateSVD of an FP32 context (tensor-core 3xTF32 projections and
+    deflations, reorthogonalised) against the FP64 oracle: three updates of
+    well-conditioned data, Omega g to 1e-6 relative."""
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = _case(2, 64, 6, 8, "f32", 4)
+    ctx = _ctx(w, 4, tol=1e-10)
+    rows = ctx.rows
+    rng = np.random.default_rng(1)
+    U = S = V = None
+    for k in range(3):
+        F = rng.standard_normal((rows, 6))
+        G = rng.standard_normal((rows, 6))
+        binding.pr_procrustes_correct(ctx, torch.tensor(F.T.copy(), device="cuda"),
+                                      torch.tensor(G.T.copy(), device="cuda"))
+        U, S, V = procrustes.update_svd(U, S, V, F, G, 1e-10)
+        g = rng.standard_normal(rows)
+        out = torch.zeros(rows, dtype=torch.float64, device="cuda")
+        rk = binding.pr_procrustes_apply(ctx, torch.tensor(g, device="cuda"), out)
+        assert rk == S.size
+        ref = U @ (V.T @ g)
+        assert np.linalg.norm(out.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref), k
+    binding.pr_check(ctx)
