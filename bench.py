@@ -50,6 +50,16 @@ ALGO_BYTES_PER_POINT_PASS = 20  # read u, u_t, kappa + write u, u_t (FP32)
 FALLBACK_HBM_GBS = 6800.0
 
 
+def hbm_passes(m_f: int, depth: int) -> int:
+    """HBM passes of one sweep of m_f steps (m_f + 1 kick levels) at `depth`
+    levels per pass; a lone final level joins the last pass at depth 8."""
+    levels = m_f + 1
+    passes = -(-levels // depth)
+    if depth == 8 and passes >= 2 and levels % depth == 1:
+        passes -= 1
+    return passes
+
+
 # ---------------------------------------------------------------- CPU oracle
 def _oracle_task(args):
     u, v, c, dt, steps, dx = args
@@ -100,6 +110,12 @@ class OracleSampler:
     def describe(self) -> str:
         return (f"{self.procs} slices x {self.steps} of {self.w.m_f} fine steps of "
                 f"{self.w.name}, one slice per process")
+
+
+def oracle_steps(w: W.Workload) -> int:
+    """Fine steps per sampled slice: about 10 s of numpy work per process
+    (64 steps of a 1024^2 slice, 8 of a 256^3 slice), at most m_F."""
+    return max(4, min(w.m_f, 64, int(1.5e8 // w.points)))
 
 
 def oracle_procs() -> int:
@@ -173,8 +189,8 @@ def measured_peak() -> tuple[float, str]:
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("paper_1905_00473_gb300/csrc/fine_tb2d.cu", "paper_1905_00473_gb300/csrc/tb_common.cuh",
-                  "paper_1905_00473_gb300/csrc/pr_internal.cuh")
+KERNEL_SOURCES = ("paper_1905_00473_gb300/csrc/tb2d_kernels.cuh", "paper_1905_00473_gb300/csrc/tb2d_sweep.cuh",
+                  "paper_1905_00473_gb300/csrc/tb_common.cuh", "paper_1905_00473_gb300/csrc/pr_internal.cuh")
 
 
 def code_only(text: str) -> str:
@@ -197,9 +213,9 @@ def kernel_source_hash(read=None) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload_key: str):
-    """DRAM bytes per fused launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+def ncu_traffic(workload_key: str, kernel: str = "fine_tb2d_kernel"):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "fine_tb2d_traffic.json")
     try:
         with open(path) as f:
@@ -207,6 +223,8 @@ def ncu_traffic(workload_key: str):
     except (OSError, ValueError):
         return None
     if d.get("source_hash") != kernel_source_hash():
+        return None
+    if not str(d.get("kernel", "fine_tb2d_kernel")).startswith(kernel):
         return None
     return d.get("per_launch_bytes", {}).get(workload_key)
 
@@ -223,10 +241,10 @@ def workload_for(cfg: str, slices: int = 0) -> W.Workload:
     time step but propagates only that many slices (small profiling runs)."""
     if cfg.startswith("4:"):   # one instance of the uneven batch, alone
         w = W.config4_instance(int(cfg[2:]))
-    elif cfg in ("2", "3"):
+    elif cfg in ("2", "3", "5"):
         w = W.CONFIGS[cfg]()
     else:
-        raise SystemExit("--config must be 2, 3 or 4:<instance> for a sweep, or 4 for the batch")
+        raise SystemExit("--config must be 2, 3, 5 or 4:<instance> for a sweep, or 4 for the batch")
     if slices and slices != w.n_slices:
         m_f = w.m_f
         w.t_final = w.t_final * slices / w.n_slices
@@ -313,7 +331,7 @@ def e2e_pipelined(binding, ctx, u_pin, v_pin, u_in, v_in, u_out, v_out, steps, b
 
 
 # ---------------------------------------------------------------- parareal vs serial fine
-def parareal_time_to_tol(dev, tol_err: float = 1e-4, k_max: int = 32, svd_tol: float = 1e-7) -> dict:
+def parareal_time_to_tol(dev, tol_err: float = 1e-4, k_max: int = 32, svd_tol: float = 1e-5) -> dict:
     """Wall time of Alg. 3 (Procrustes corrector, pr_iterate) to a relative
     energy-norm error <= tol_err at T against the serial fine solution, and
     the serial fine solve itself (the same fine kernels, one slice after the
@@ -356,12 +374,13 @@ def parareal_time_to_tol(dev, tol_err: float = 1e-4, k_max: int = 32, svd_tol: f
                              ref[N].contiguous(), refv[N].contiguous(), tol_err)
     t_par = 1e3 * (time.perf_counter() - t0)
     phases = binding.pr_iterate_phases(ctx)
+    corr = binding.pr_iterate_corrector_phases(ctx)
     reached = out["err"] and out["err"][-1] <= tol_err
     return {"workload": w.name, "corrector": "procrustes", "svd_tol": svd_tol, "tol_err": tol_err,
             "serial_fine_ms": t_serial, "parareal_ms": t_par, "iterations": out["k_done"],
             "reached": bool(reached),
             "speedup_vs_serial_fine": (t_serial / t_par) if reached else None,
-            "phases_ms": phases,
+            "phases_ms": phases, "corrector_breakdown": corr,
             "err_hist": out["err"], "rank_hist": out["rank"],
             "note": "pr_iterate wall time, host-synchronised, stopping at the first iteration "
                     "within tol_err of the serial fine solution computed by the same fine "
@@ -430,7 +449,7 @@ def run_reference(a) -> int:
         return 0
     w = workload_for(a.config, a.slices)
     procs = oracle_procs()
-    steps_per_sample = max(4, min(w.m_f, 64))
+    steps_per_sample = oracle_steps(w)
     smp = OracleSampler(w, procs, steps_per_sample)
     try:
         for _ in range(a.warmup):
@@ -466,7 +485,7 @@ def run_ours(a) -> int:
     # the oracle pool is spawned before any CUDA call
     smp = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        smp = OracleSampler(w, oracle_procs(), max(4, min(w.m_f, 64)))
+        smp = OracleSampler(w, oracle_procs(), oracle_steps(w))
 
     import torch
     from paper_1905_00473_gb300 import binding
@@ -491,6 +510,7 @@ def run_ours(a) -> int:
                             block_depth=a.block_depth)
     if a.columns:
         binding.pr_set_fused_columns(ctx, a.columns)
+    binding.pr_set_one_launch(ctx, a.one_launch == "on")
     info = binding.pr_info(ctx)
     u_in = u_pin.to(dev)
     v_in = v_pin.to(dev)
@@ -537,6 +557,7 @@ def run_ours(a) -> int:
     binding.pr_check(ctx)
     fused_n, fused_ms = binding.pr_profile_read(ctx, 0)
     single_n, single_ms = binding.pr_profile_read(ctx, 1)
+    sweep_n, sweep_ms = binding.pr_profile_read(ctx, 2)
     ms = sharding.max_over_ranks(ms, device=dev)
     l2_note = (f"L2 flushed between timed steps ({flush_buf.numel() * 4 >> 20} MiB write), "
                f"steps timed one by one" if flush else
@@ -555,20 +576,27 @@ def run_ours(a) -> int:
 
     # roofline of the dominant kernel (fused pass when present)
     peak, peak_src = measured_peak()
-    if fused_n > 0:
-        kname, launches, kms = "fine_tb2d_kernel", fused_n, fused_ms
-        levels_per_launch = info["block_depth"]
+    passes = hbm_passes(w.m_f, info["block_depth"])
+    if sweep_n > 0:
+        # every pass of the sweep in one persistent launch
+        kname, launches, kms = "fine_tb2d_sweep_kernel", sweep_n, sweep_ms
+        levels_per_launch, passes_per_launch = w.m_f + 1, passes
+    elif fused_n > 0:
+        kname = "fine_tb3d_kernel" if w.dim == 3 else "fine_tb2d_kernel"
+        launches, kms = fused_n, fused_ms
+        levels_per_launch, passes_per_launch = info["block_depth"], 1
     else:
         kname, launches, kms = "level_f32 (one level per launch)", single_n, single_ms
-        levels_per_launch = 1
-    per_launch_bytes = ALGO_BYTES_PER_POINT_PASS * w.points * w.n_slices
+        levels_per_launch, passes_per_launch = 1, 1
+    per_launch_bytes = ALGO_BYTES_PER_POINT_PASS * w.points * w.n_slices * passes_per_launch
     avg_ms = kms / max(1, launches)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src,
-            "traffic": ncu_traffic(w.name) if fused_n > 0 else None,
+            "traffic": ncu_traffic(w.name, kname) if (w.dim == 2 and (fused_n > 0 or sweep_n > 0)) else None,
             "algorithmic_bytes_per_launch": per_launch_bytes,
-            "levels_per_launch": levels_per_launch, "mean_launch_ms": avg_ms,
+            "levels_per_launch": levels_per_launch, "hbm_passes_per_launch": passes_per_launch,
+            "mean_launch_ms": avg_ms,
             "launch_share": kms / ms if ms > 0 else None}
 
     cpu = None
@@ -593,13 +621,14 @@ def run_ours(a) -> int:
             "data": "synthetic",
             "config": dict(workload_desc(w), l2=l2_note, block_depth=info["block_depth"],
                            columns_per_thread=a.columns or "library default",
+                           launches_per_sweep="one" if sweep_n > 0 else "one per pass",
                            parallelism=f"replica per GPU x{world}"),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "point-updates/s", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes, "steps": e2e_steps, "warmup": max(E2E_BUFFERS, a.warmup),
                     "mode": e2e_mode},
-            "gpu_launches": fused_n + single_n,
+            "gpu_launches": fused_n + single_n + sweep_n,
             "clocks": clk,
             "parareal": par,
         }
@@ -616,7 +645,7 @@ def main(argv=None) -> int:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="3",
-                    help="2, 3: the sweep workloads; 4: the uneven batch; 4:<i>: instance i of the batch alone")
+                    help="2, 3, 5: the sweep workloads; 4: the uneven batch; 4:<i>: instance i of the batch alone")
     ap.add_argument("--block-depth", type=int, default=0, help="0 = library default")
     ap.add_argument("--columns", type=int, default=0, choices=[0, 2, 4],
                     help="fused-kernel columns per thread (0 = library default)")
@@ -626,6 +655,8 @@ def main(argv=None) -> int:
     ap.add_argument("--instances", type=int, default=8, help="--config 4: instances in the batch")
     ap.add_argument("--no-parareal", action="store_true",
                     help="skip the parareal time-to-1e-4 measurement")
+    ap.add_argument("--one-launch", choices=["on", "off"], default="on",
+                    help="on: a whole sweep in one persistent launch where supported; off: one launch per pass")
     ap.add_argument("--l2-flush", choices=["auto", "on", "off"], default="auto",
                     help="auto: flush L2 between timed steps when the inputs are smaller than 2x L2")
     a = ap.parse_args(argv)

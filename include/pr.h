@@ -156,7 +156,11 @@ pr_status pr_coarse_sweep(pr_ctx* ctx, const void* u, const void* v, void* U_out
  *  k_done      HOST int or NULL: iterations done.
  * Fine sweeps run in the context dtype; Lambda, Omega, Lambda^dagger, I, the
  * data matrices and the SVD in FP64 (cuFFT, cuBLAS, cuSOLVER for the FFTs and
- * the dense factorisations).  The correction of a slice is applied to the
+ * the dense factorisations).  In FP32 contexts the tall products of UpdateSVD
+ * with the kept bases run on the tensor cores in 3xTF32 (see
+ * pr_snapshot_project) with one reorthogonalisation pass, and the SVD of the
+ * small matrix H is taken from the symmetric eigenproblem of H^T H when every
+ * kept singular value is at least 1e-6 of the largest (else FP64 gesvd).  The correction of a slice is applied to the
  * difference Lambda w - Lambda U_n with zero mode sum w - sum U_n, which by
  * linearity equals Alg. 3's two applications.  Synchronises the stream.
  * Reads the device-side error flags of the fine and coarse sweeps after every
@@ -178,6 +182,18 @@ pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int K, int cor
  *  ms   HOST double[4], written (zeros before the first pr_iterate).
  * Timed with CUDA events on the call's stream.  PR_EINVAL for NULL pointers. */
 pr_status pr_iterate_phases(const pr_ctx* ctx, double* ms);
+
+/* pr_iterate_corrector_phases -- device time of "creating the corrector" in
+ * the last pr_iterate call (Procrustes), split per step of Alg. 1 and summed
+ * over the iterations: ms[0] projections and deflations of the new data
+ * against the kept bases, ms[1] reduced QR of the residual blocks, ms[2] the
+ * small matrix H and its SVD, ms[3] the basis rotation, ms[4] the residual
+ * ||F - Omega G|| / ||F|| of the iteration's data.  *eig_svds (may be NULL)
+ * receives how many of the *svds SVDs (may be NULL) were taken through the
+ * symmetric eigenproblem of H^T H (FP32 contexts, when every kept singular
+ * value is at least 1e-6 of the largest; otherwise FP64 gesvd).
+ *  ms   HOST double[5], written.  PR_EINVAL for NULL ctx or ms. */
+pr_status pr_iterate_corrector_phases(const pr_ctx* ctx, double* ms, int* eig_svds, int* svds);
 
 /* pr_procrustes_correct -- UpdateSVD (Alg. 1): M <- M + F G^T with the
  * context's truncated SVD M = X Sigma Y^T (rank cut sigma_i/sigma_max > tol).
@@ -241,6 +257,33 @@ pr_status pr_snapshot_deflate(pr_ctx* ctx, const double* A, int64_t lda, const d
                               const double* F, int64_t ldf, int64_t M, int64_t K, int N, double* O,
                               int64_t ldo, void* stream);
 
+/* pr_iterate_adjoint -- reverse mode through K iterations of Alg. 3 (the
+ * parareal solve itself, not only its K = N limit) with every iteration's
+ * phase corrector Omega^k = X_k Y_k^T frozen at the value the forward run
+ * computes from its data (Alg. 1).  The paper does not differentiate its
+ * method; with the correctors frozen the map (u0, p0, c) -> u^{K+1}_N is a
+ * composition of F, C (Sec. 3.1), R, I (Sec. 6), Lambda, Lambda^dagger
+ * (Sec. 3.4, Alg. 2) and fixed matrices, and this call applies the
+ * transposes of those maps in reverse order.
+ *  u0, p0      initial state [n^d] (dtype, device); the forward run is
+ *              pr_iterate(ctx, u0, p0, K, corrector, ...) without early stop.
+ *  K           iterations, 1 <= K (K = N gives the serial fine gradient).
+ *  corrector   PR_CORR_*.
+ *  gu_T, gv_T  dL/du, dL/du_t of the loss at the state u^{K+1}_N [n^d].
+ *  gc          dL/dc at the fine nodes [n^d] (the coarse c is R c, so its
+ *              terms are scattered back onto the coarse nodes); includes the
+ *              dependence of Lambda (c^-1 u_t) and Lambda^dagger (c p) on c.
+ *  gu0, gp0    dL/du0, dL/dp0 [n^d].
+ * Every iteration's states are kept ((K+1)(N+1) fine states, allocated and
+ * freed by the call); each slice of F and C is recomputed from its start
+ * state in the reverse sweep.  The propagators' transposes run in the
+ * context dtype with dL/dkappa in FP64; the correction-path transposes in
+ * FP64.  Synchronises the stream.  PR_ETIMEOUT if a bounded wait of the
+ * forward run gave up. */
+pr_status pr_iterate_adjoint(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector,
+                             const void* gu_T, const void* gv_T, void* gc, void* gu0, void* gp0,
+                             void* stream);
+
 /* ---- batches of independent instances of uneven sizes ------------------- */
 typedef struct pr_batch pr_batch;
 
@@ -284,6 +327,15 @@ void pr_batch_destroy(pr_batch* b);
  * Takes effect at the next call. */
 pr_status pr_set_fused_columns(pr_ctx* ctx, int columns);
 
+/* pr_set_one_launch -- on != 0 (the default): where the fused 2D kernel runs
+ * whole rows at depth 8 with four columns per thread (n = 128 .. 1024) and a
+ * sweep takes at least two passes, pr_fine_all_slices runs every pass of the
+ * sweep (all slices) in ONE persistent cooperative launch, one CTA per SM, with
+ * a bounded grid-wide barrier between passes; on == 0: one launch per pass.
+ * Both compute the same level recurrence in the same order (bit-identical
+ * results).  Takes effect at the next call. */
+pr_status pr_set_one_launch(pr_ctx* ctx, int on);
+
 /* pr_debug_stall_waits -- test hook for the time-out path.  While enabled,
  * fused-kernel launches of this context expect more bulk-copy bytes than
  * they issue, so each bounded shared-memory barrier wait runs out (after
@@ -321,8 +373,9 @@ pr_status pr_energy(pr_ctx* ctx, const void* u, const void* v, int n_begin, int 
 pr_status pr_profile(pr_ctx* ctx, int on);
 
 /* pr_profile_read -- synchronise on the recorded events and report, for
- * kernel kind 0 (fused multi-level pass) or 1 (single-level pass), the number
- * of launches recorded and their summed duration in milliseconds. */
+ * kernel kind 0 (fused multi-level pass), 1 (single-level pass) or 2 (a whole
+ * sweep in one launch, pr_set_one_launch), the number of launches recorded
+ * and their summed duration in milliseconds. */
 pr_status pr_profile_read(pr_ctx* ctx, int kind, int* launches, double* total_ms);
 
 /* Size in bytes of the fixed device scratch array behind

@@ -73,9 +73,15 @@ _SIGNATURES = {
     "pr_set_fused_columns": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_batch_destroy": (None, [_P]),
     "pr_debug_stall_waits": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pr_set_one_launch": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double)]),
+    "pr_iterate_corrector_phases": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                                   ctypes.POINTER(ctypes.c_int),
+                                                   ctypes.POINTER(ctypes.c_int)]),
+    "pr_iterate_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
+                                          _P, _P]),
     "pr_snapshot_project": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64,
                                            ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _P,
                                            ctypes.c_int64, _P]),
@@ -416,3 +422,33 @@ def pr_snapshot_deflate(ctx: Context, A, T, F, O, stream=None) -> None:
     po, ldo = _f64_matrix("O", O, M, N)
     _check(load().pr_snapshot_deflate(ctx.handle, pa, lda, pt, ldt, pf, ldf, M, K, N, po, ldo,
                                       ctypes.c_void_p(_stream_ptr(stream))), ctx.handle)
+
+
+def pr_iterate_corrector_phases(ctx: Context) -> dict:
+    """Device time (ms) of the steps of creating the corrector in the last
+    pr_iterate call, and how many SVDs went through the eigenproblem path."""
+    ms = (ctypes.c_double * 5)()
+    ne, na = ctypes.c_int(), ctypes.c_int()
+    _check(load().pr_iterate_corrector_phases(ctx.handle, ms, ctypes.byref(ne), ctypes.byref(na)),
+           ctx.handle)
+    keys = ("project_deflate_ms", "qr_ms", "h_svd_ms", "rotate_ms", "residual_ms")
+    out = {k: ms[i] for i, k in enumerate(keys)}
+    out["eig_svds"], out["svds"] = ne.value, na.value
+    return out
+
+
+def pr_iterate_adjoint(ctx: Context, u0, p0, K: int, corrector: int, gu_T, gv_T, gc, gu0, gp0,
+                       stream=None) -> None:
+    """Reverse mode through K iterations of Alg. 3 with the correctors frozen:
+    writes dL/dc, dL/du0, dL/dp0 for dL/du, dL/du_t at u^{K+1}_N."""
+    pts = ctx.n ** ctx.dim
+    st = load().pr_iterate_adjoint(ctx.handle, ctx._arr(u0, "u0", pts), ctx._arr(p0, "p0", pts), K,
+                                   corrector, ctx._arr(gu_T, "gu_T", pts), ctx._arr(gv_T, "gv_T", pts),
+                                   ctx._arr(gc, "gc", pts), ctx._arr(gu0, "gu0", pts),
+                                   ctx._arr(gp0, "gp0", pts), ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, ctx.handle)
+
+
+def pr_set_one_launch(ctx: Context, on: bool) -> None:
+    """Whole sweep in one persistent launch (default) or one launch per pass."""
+    _check(load().pr_set_one_launch(ctx.handle, 1 if on else 0), ctx.handle)

@@ -252,7 +252,94 @@ pr_status run(pr_ctx* ctx, const T* u0, const T* p0, const T* guT, const T* gvT,
     return PR_OK;
 }
 
+// Reverse of ONE slice of context c (fine or coarse) from its start state
+// (u_in, v_in): recompute the slice's trace, then the m + 1 transposed
+// levels, with (lu, lv) the adjoints of the slice's end state on entry and of
+// its start state on return; dL/dkappa accumulates into gk (FP64, [pts]).
+template <typename T, int DIM>
+pr_status slice_adjoint_t(pr_ctx* c, const T* u_in, const T* v_in, T* lu, T* lv, double* gk, cudaStream_t st) {
+    const int64_t pts = c->pts, n = c->n;
+    const int m = c->m_f;
+    const size_t fb = (size_t)pts * sizeof(T);
+    // workspace: trace (m+1), v, two adjoint fields
+    const size_t need = (size_t)((m + 1) + 1 + 2) * fb;
+    if (need > c->sadj_bytes) {
+        cudaError_t e = cudaStreamSynchronize(st);   // the old workspace may still be in use
+        if (e != cudaSuccess) return pr_cuda_fail(c, e, "slice adjoint: synchronize");
+        cudaFree(c->sadj_ws);
+        c->sadj_ws = nullptr;
+        c->sadj_bytes = 0;
+        e = cudaMalloc(&c->sadj_ws, need);
+        if (e != cudaSuccess) return pr_cuda_fail(c, e, "slice adjoint: workspace");
+        c->sadj_bytes = need;
+    }
+    T* tr = (T*)c->sadj_ws;
+    T* vw = tr + (size_t)(m + 1) * pts;
+    T* la = vw + pts;
+    T* lb = vw + 2 * pts;
+    const T* kap = (const T*)c->kappa;
+    const T dt = (T)c->dt_f;
+    auto w_of = [&](int g) { return (T)((g == 0 || g == m) ? 0.5 : 1.0); };
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const bool quads = sizeof(T) == 4 && n % 4 == 0;
+    dim3 grid, block;
+    rows::shape_for(quads ? n / 4 : n, pts / n, sms > 0 ? sms : 1, &grid, &block);
+    cudaMemcpyAsync(tr, u_in, fb, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(vw, v_in, fb, cudaMemcpyDeviceToDevice, st);
+    for (int g = 0; g <= m; ++g) {
+        const T* u = tr + (size_t)g * pts;
+        T* un = tr + (size_t)(g + 1 <= m ? g + 1 : g) * pts;
+        if constexpr (sizeof(T) == 4) {
+            if (quads) {
+                fwd_level_x4<DIM><<<grid, block, 0, st>>>(u, vw, un, kap, n, pts, w_of(g), dt, g < m);
+                continue;
+            }
+        }
+        fwd_level<T, DIM><<<grid, block, 0, st>>>(u, vw, un, kap, n, pts, w_of(g), dt, g < m);
+    }
+    // reverse: (lu, lv) -> la/lb ping-pong -> back into (lu, lv)
+    T* src_u = lu;
+    T* src_v = lv;
+    for (int g = m; g >= 0; --g) {
+        T* du = ((m - g) % 2 == 0) ? la : lu;
+        T* dv = ((m - g) % 2 == 0) ? lb : lv;
+        const T* ug = tr + (size_t)g * pts;
+        if constexpr (sizeof(T) == 4) {
+            if (quads) {
+                adj_level_x4<DIM><<<grid, block, 0, st>>>(src_u, src_v, ug, kap, du, dv, gk, n, pts, w_of(g), dt, g < m);
+                src_u = du;
+                src_v = dv;
+                continue;
+            }
+        }
+        adj_level<T, DIM><<<grid, block, 0, st>>>(src_u, src_v, ug, kap, du, dv, gk, n, pts, w_of(g), dt, g < m);
+        src_u = du;
+        src_v = dv;
+    }
+    if (src_u != lu) {
+        cudaMemcpyAsync(lu, src_u, fb, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(lv, src_v, fb, cudaMemcpyDeviceToDevice, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return pr_cuda_fail(c, e, "slice adjoint: launch");
+    return PR_OK;
+}
+
 }  // namespace
+
+pr_status pr_slice_adjoint(pr_ctx* c, const void* u_in, const void* v_in, void* lu, void* lv, double* gk,
+                           cudaStream_t st) {
+    const bool f32 = c->dtype == PR_F32;
+    switch (c->dim) {
+        case 1: return f32 ? slice_adjoint_t<float, 1>(c, (const float*)u_in, (const float*)v_in, (float*)lu, (float*)lv, gk, st)
+                           : slice_adjoint_t<double, 1>(c, (const double*)u_in, (const double*)v_in, (double*)lu, (double*)lv, gk, st);
+        case 2: return f32 ? slice_adjoint_t<float, 2>(c, (const float*)u_in, (const float*)v_in, (float*)lu, (float*)lv, gk, st)
+                           : slice_adjoint_t<double, 2>(c, (const double*)u_in, (const double*)v_in, (double*)lu, (double*)lv, gk, st);
+        default: return f32 ? slice_adjoint_t<float, 3>(c, (const float*)u_in, (const float*)v_in, (float*)lu, (float*)lv, gk, st)
+                            : slice_adjoint_t<double, 3>(c, (const double*)u_in, (const double*)v_in, (double*)lu, (double*)lv, gk, st);
+    }
+}
 
 extern "C" pr_status pr_adjoint(pr_ctx* ctx, const void* u0, const void* p0, const void* gu_T,
                                 const void* gv_T, void* gc, void* gu0, void* gp0, void* stream) {

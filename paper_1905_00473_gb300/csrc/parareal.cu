@@ -69,13 +69,17 @@ __global__ void restrict_kernel(const T* __restrict__ u, const T* __restrict__ v
 // out[DIM*cpts + J] = W_t / c; W is sampled at coarse nodes of an array with
 // `stride`-spaced nodes (stride = ratio reads R u straight from a fine array,
 // stride = 1 a coarse array).  sign = +1 writes, -1 subtracts (Lambda w - Lambda U).
-__constant__ double c_beta[4];
+// central first-derivative weights beta_1..beta_h of nabla_h (Sec. 3.4),
+// passed by value so that contexts of different orders never share them
+struct Beta {
+    double b[4];
+};
 
 template <typename T, int DIM>
 __global__ void lambda_kernel(const T* __restrict__ w, const T* __restrict__ wt,
                               const double* __restrict__ cc, double* __restrict__ out,
                               int64_t nc, int stride, int64_t arr_n, int64_t arr_pts, int64_t cpts,
-                              int order_half, double inv_dx, double sign, int nslices,
+                              int order_half, Beta beta, double inv_dx, double sign, int nslices,
                               int64_t out_ld) {
     const int64_t total = (int64_t)nslices * cpts;
     for (int64_t idx = (int64_t)blockIdx.x * kT + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * kT) {
@@ -98,7 +102,7 @@ __global__ void lambda_kernel(const T* __restrict__ w, const T* __restrict__ wt,
                 const int64_t cp = (c[a] + k) % nc, cm = (c[a] - k + nc) % nc;
                 const double up = (double)ws[base + (cp * stride - f[a]) * astride];
                 const double um = (double)ws[base + (cm * stride - f[a]) * astride];
-                acc += c_beta[k - 1] * (up - um);
+                acc += beta.b[k - 1] * (up - um);
             }
             const double g = acc * inv_dx;
             if (sign > 0) o[a * cpts + J] = g;
@@ -272,6 +276,25 @@ __global__ void add_diag(double* __restrict__ H, int64_t ld, const double* __res
     for (int i = blockIdx.x * kT + threadIdx.x; i < s; i += gridDim.x * kT) H[(int64_t)i * ld + i] += S[i];
 }
 
+// V(:, i) = E(:, h-1-i) for i < r (eigenvectors of ascending eigenvalues,
+// reordered by descending singular value)
+__global__ void reverse_cols(const double* __restrict__ E, double* __restrict__ V, int h, int r) {
+    for (int64_t idx = (int64_t)blockIdx.x * kT + threadIdx.x; idx < (int64_t)h * r; idx += (int64_t)gridDim.x * kT) {
+        const int col = (int)(idx / h), row = (int)(idx - (int64_t)col * h);
+        V[idx] = E[(int64_t)(h - 1 - col) * h + row];
+    }
+}
+// sign of R_ii of a geqrf result (ld h), for i < r
+__global__ void diag_sign(const double* __restrict__ A, int h, int r, double* __restrict__ sg) {
+    for (int i = blockIdx.x * kT + threadIdx.x; i < r; i += gridDim.x * kT) sg[i] = A[(int64_t)i * h + i] < 0 ? -1.0 : 1.0;
+}
+// X(:, i) = Q(:, i) sg[i]
+__global__ void scale_cols(const double* __restrict__ Q, const double* __restrict__ sg, double* __restrict__ X, int h,
+                           int r) {
+    for (int64_t idx = (int64_t)blockIdx.x * kT + threadIdx.x; idx < (int64_t)h * r; idx += (int64_t)gridDim.x * kT)
+        X[idx] = Q[idx] * sg[idx / h];
+}
+
 int blocks_for(int64_t m) {
     int64_t b = (m + kT - 1) / kT;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
@@ -312,9 +335,31 @@ struct pr_driver {
     double *UF = nullptr, *VG = nullptr, *A1 = nullptr, *A2 = nullptr, *H = nullptr;
     double *Xh = nullptr, *YhT = nullptr, *sig = nullptr, *work = nullptr, *rwork = nullptr;
     double *F2 = nullptr, *G2 = nullptr;            // copies of F, G for the residual
+    double *E = nullptr, *tauh = nullptr, *rsign = nullptr;   // SVD through the eigenproblem of H^T H
+    // a second lane (stream, handles, scratch) on which G's projections,
+    // deflations and QR run beside F's: those steps are latency-bound
+    cudaStream_t st2 = nullptr;
+    cublasHandle_t blas2 = nullptr;
+    cusolverDnHandle_t sol2 = nullptr;
+    double *Tb2 = nullptr, *work2 = nullptr, *tau2 = nullptr;
+    int64_t work2_len = 0;
+    int* info2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int* info = nullptr;
     int64_t work_len = 0;
     int hcap = 0;   // allocated (s+N) capacity of the small matrices
+    // FP32 contexts: the tall-skinny products with the bases (projections
+    // and deflations of Alg. 1) run on the tensor cores in 3xTF32
+    // (gram_tc.cu), with one reorthogonalisation pass; FP64 contexts use
+    // FP64 DGEMM throughout
+    bool tc = false;
+    Beta beta = {{0.0, 0.0, 0.0, 0.0}};   // nabla_h weights of this context's order
+    int eig_svds = 0, all_svds = 0;        // SVDs taken by svd_eig_, and all, since the last pr_iterate
+    // per-call breakdown of creating the corrector (pr_iterate_corrector_phases):
+    // projections and deflations, QR of the residual blocks, H and its SVD,
+    // basis rotation, residual diagnostic
+    cudaEvent_t cev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double corr_ms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     // phase timers of the last pr_iterate (Sec. 7.2.4 table columns): initial
     // coarse sweep, parallel computation, creating the corrector, serial update
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -332,12 +377,20 @@ void pr_driver_free(pr_ctx* ctx) {
     }
     if (d->blas) cublasDestroy(d->blas);
     if (d->sol) cusolverDnDestroy(d->sol);
+    if (d->blas2) cublasDestroy(d->blas2);
+    if (d->sol2) cusolverDnDestroy(d->sol2);
+    if (d->st2) cudaStreamDestroy(d->st2);
+    if (d->ev_fork) cudaEventDestroy(d->ev_fork);
+    if (d->ev_join) cudaEventDestroy(d->ev_join);
     for (cudaEvent_t e : d->ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : d->cev)
         if (e) cudaEventDestroy(e);
     void* bufs[] = {d->vF_u, d->vF_v, d->Uc_u, d->Uc_v, d->w_u, d->w_v, d->Fm, d->Gm, d->dvec, d->gvec,
                     d->du, d->dut, d->zero, d->zc, d->zf, d->Xb, d->Yb, d->WX, d->WY, d->WXn, d->WYn,
                     d->Tb, d->vb, d->S, d->QF, d->QG, d->RF, d->RG, d->tau, d->UF, d->VG, d->A1, d->A2,
-                    d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork, d->F2, d->G2, d->info};
+                    d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork, d->F2, d->G2, d->info, d->E, d->tauh,
+                    d->rsign, d->Tb2, d->work2, d->tau2, d->info2};
     for (void* b : bufs) cudaFree(b);
     delete d;
     ctx->drv = nullptr;
@@ -397,6 +450,8 @@ pr_status driver(pr_ctx* ctx, cudaStream_t st, pr_driver** out) {
         PR_TRY_ST(alloc(ctx, (void**)&d->zc, (size_t)std::max(d->dim, 2) * d->cpts * 16, "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->zf, (size_t)2 * d->pts * 16, "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->info, sizeof(int), "driver: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&d->info2, sizeof(int), "driver: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&d->tau2, (size_t)d->N * 8, "driver: alloc"));
         int nn[3], nf[3];
         for (int a = 0; a < d->dim; ++a) {
             nn[a] = (int)d->nc;
@@ -407,6 +462,15 @@ pr_status driver(pr_ctx* ctx, cudaStream_t st, pr_driver** out) {
         PR_FFT(ctx, cufftPlanMany(&d->plan_c2, d->dim, nn, nullptr, 1, (int)d->cpts, nullptr, 1, (int)d->cpts, CUFFT_Z2Z, 2), "plan");
         PR_FFT(ctx, cufftPlanMany(&d->plan_f2, d->dim, nf, nullptr, 1, (int)d->pts, nullptr, 1, (int)d->pts, CUFFT_Z2Z, 2), "plan");
         d->have_plans = true;
+        d->tc = ctx->dtype == PR_F32;
+        for (int i = 0; i < 6; ++i) PR_CUDA_TRY(ctx, cudaEventCreate(&d->cev[i]));
+        PR_CUDA_TRY(ctx, cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming));
+        PR_CUDA_TRY(ctx, cudaEventCreateWithFlags(&d->ev_join, cudaEventDisableTiming));
+        PR_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&d->st2, cudaStreamNonBlocking));
+        PR_BLAS(ctx, cublasCreate(&d->blas2), "cublasCreate");
+        PR_BLAS(ctx, cusolverDnCreate(&d->sol2), "cusolverDnCreate");
+        PR_BLAS(ctx, cublasSetStream(d->blas2, d->st2), "cublasSetStream");
+        PR_BLAS(ctx, cusolverDnSetStream(d->sol2, d->st2), "cusolverDnSetStream");
         PR_BLAS(ctx, cublasCreate(&d->blas), "cublasCreate");
         PR_BLAS(ctx, cusolverDnCreate(&d->sol), "cusolverDnCreate");
         // central first-derivative weights of order 2*h (Sec. 3.4 beta_j form)
@@ -417,8 +481,7 @@ pr_status driver(pr_ctx* ctx, cudaStream_t st, pr_driver** out) {
             case 6: beta[0] = 0.75; beta[1] = -0.15; beta[2] = 1.0 / 60.0; break;
             default: beta[0] = 0.8; beta[1] = -0.2; beta[2] = 4.0 / 105.0; beta[3] = -1.0 / 280.0; break;
         }
-        cudaError_t e = cudaMemcpyToSymbol(c_beta, beta, sizeof beta);
-        if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "driver: upload beta");
+        for (int k = 0; k < 4; ++k) d->beta.b[k] = beta[k];
     }
     pr_driver* d = ctx->drv;
     PR_FFT(ctx, cufftSetStream(d->plan_c1, st), "set stream");
@@ -456,9 +519,9 @@ void launch_lambda_t(pr_ctx* ctx, const void* w, const void* wt, double* out, in
     const int h = ctx->opts.grad_order / 2;
     const double inv_dx = 1.0 / ctx->coarse->dx;
     switch (ctx->dim) {
-        case 1: lambda_kernel<T, 1><<<blocks_for(total), kT, 0, st>>>((const T*)w, (const T*)wt, ctx->coarse->c64, out, nc, stride, arr_n, arr_pts, cpts, h, inv_dx, sign, ns, out_ld); break;
-        case 2: lambda_kernel<T, 2><<<blocks_for(total), kT, 0, st>>>((const T*)w, (const T*)wt, ctx->coarse->c64, out, nc, stride, arr_n, arr_pts, cpts, h, inv_dx, sign, ns, out_ld); break;
-        default: lambda_kernel<T, 3><<<blocks_for(total), kT, 0, st>>>((const T*)w, (const T*)wt, ctx->coarse->c64, out, nc, stride, arr_n, arr_pts, cpts, h, inv_dx, sign, ns, out_ld); break;
+        case 1: lambda_kernel<T, 1><<<blocks_for(total), kT, 0, st>>>((const T*)w, (const T*)wt, ctx->coarse->c64, out, nc, stride, arr_n, arr_pts, cpts, h, ctx->drv->beta, inv_dx, sign, ns, out_ld); break;
+        case 2: lambda_kernel<T, 2><<<blocks_for(total), kT, 0, st>>>((const T*)w, (const T*)wt, ctx->coarse->c64, out, nc, stride, arr_n, arr_pts, cpts, h, ctx->drv->beta, inv_dx, sign, ns, out_ld); break;
+        default: lambda_kernel<T, 3><<<blocks_for(total), kT, 0, st>>>((const T*)w, (const T*)wt, ctx->coarse->c64, out, nc, stride, arr_n, arr_pts, cpts, h, ctx->drv->beta, inv_dx, sign, ns, out_ld); break;
     }
 }
 void lambda_(pr_ctx* ctx, const void* w, const void* wt, double* out, int stride, int64_t arr_n,
@@ -553,6 +616,10 @@ pr_status ensure_capacity(pr_ctx* ctx, pr_driver* d, int need_s, int ncols, cuda
                          cudaMemcpyDeviceToDevice);
             cudaMemcpy(S, d->S, (size_t)d->s * 8, cudaMemcpyDeviceToDevice);
         }
+        double* Tb2 = nullptr;
+        PR_TRY_ST(alloc(ctx, (void**)&Tb2, (size_t)bc * d->N * 8, "svd: alloc"));
+        cudaFree(d->Tb2);
+        d->Tb2 = Tb2;
         double** olds[] = {&d->Xb, &d->Yb, &d->WX, &d->WY, &d->WXn, &d->WYn, &d->Tb, &d->vb, &d->S};
         for (double** o : olds) cudaFree(*o);
         d->Xb = Xb; d->Yb = Yb; d->WX = WX; d->WY = WY; d->WXn = WXn; d->WYn = WYn;
@@ -562,7 +629,8 @@ pr_status ensure_capacity(pr_ctx* ctx, pr_driver* d, int need_s, int ncols, cuda
     const int h = need_s;   // (s + ncols)
     if (h > d->hcap || !d->QF) {
         const int hc = std::max(h, d->hcap * 2);
-        double** smalls[] = {&d->RF, &d->RG, &d->UF, &d->VG, &d->A1, &d->A2, &d->H, &d->Xh, &d->YhT};
+        double** smalls[] = {&d->RF, &d->RG, &d->UF, &d->VG, &d->A1, &d->A2, &d->H, &d->Xh, &d->YhT,
+                             &d->E, &d->tauh, &d->rsign};
         for (double** p : smalls) {
             cudaFree(*p);
             *p = nullptr;
@@ -577,12 +645,41 @@ pr_status ensure_capacity(pr_ctx* ctx, pr_driver* d, int need_s, int ncols, cuda
         PR_TRY_ST(alloc(ctx, (void**)&d->H, (size_t)hc * hc * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->Xh, (size_t)hc * hc * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->YhT, (size_t)hc * hc * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&d->E, (size_t)hc * hc * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&d->tauh, (size_t)hc * 8, "svd: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&d->rsign, (size_t)hc * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->sig, (size_t)hc * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->rwork, (size_t)hc * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->tau, (size_t)ncols * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->QF, (size_t)rows * ncols * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->QG, (size_t)rows * ncols * 8, "svd: alloc"));
         d->hcap = hc;
+    }
+    return PR_OK;
+}
+
+// One lane of the UpdateSVD products: its stream, library handles and scratch.
+struct Lane {
+    cudaStream_t st;
+    cublasHandle_t blas;
+    cusolverDnHandle_t sol;
+    double* Tb;
+    double** work;
+    int64_t* work_len;
+    double* tau;
+    int* info;
+};
+Lane lane_f(pr_driver* d, cudaStream_t st) { return {st, d->blas, d->sol, d->Tb, &d->work, &d->work_len, d->tau, d->info}; }
+Lane lane_g(pr_driver* d) { return {d->st2, d->blas2, d->sol2, d->Tb2, &d->work2, &d->work2_len, d->tau2, d->info2}; }
+
+pr_status ensure_lane_work(pr_ctx* ctx, const Lane& L, int64_t need) {
+    if (need > *L.work_len) {
+        cudaError_t e = cudaStreamSynchronize(L.st);
+        if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "svd: synchronize");
+        cudaFree(*L.work);
+        *L.work = nullptr;
+        PR_TRY_ST(alloc(ctx, (void**)L.work, (size_t)need * 8, "svd: alloc work"));
+        *L.work_len = need;
     }
     return PR_OK;
 }
@@ -598,15 +695,15 @@ pr_status ensure_work(pr_ctx* ctx, pr_driver* d, int64_t need) {
 }
 
 // reduced QR of A (rows x nc, overwritten): Q in A, R (nc x nc) in Rout
-pr_status qr_(pr_ctx* ctx, pr_driver* d, double* A, double* Rout, int nc, cudaStream_t st) {
+pr_status qr_(pr_ctx* ctx, pr_driver* d, const Lane& L, double* A, double* Rout, int nc) {
     const int m = (int)d->rows;
     int l1 = 0, l2 = 0;
-    PR_BLAS(ctx, cusolverDnDgeqrf_bufferSize(d->sol, m, nc, A, m, &l1), "geqrf size");
-    PR_BLAS(ctx, cusolverDnDorgqr_bufferSize(d->sol, m, nc, nc, A, m, d->tau, &l2), "orgqr size");
-    PR_TRY_ST(ensure_work(ctx, d, std::max(l1, l2)));
-    PR_BLAS(ctx, cusolverDnDgeqrf(d->sol, m, nc, A, m, d->tau, d->work, (int)d->work_len, d->info), "geqrf");
-    extract_r<<<blocks_for((int64_t)nc * nc), kT, 0, st>>>(A, Rout, m, nc);
-    PR_BLAS(ctx, cusolverDnDorgqr(d->sol, m, nc, nc, A, m, d->tau, d->work, (int)d->work_len, d->info), "orgqr");
+    PR_BLAS(ctx, cusolverDnDgeqrf_bufferSize(L.sol, m, nc, A, m, &l1), "geqrf size");
+    PR_BLAS(ctx, cusolverDnDorgqr_bufferSize(L.sol, m, nc, nc, A, m, L.tau, &l2), "orgqr size");
+    PR_TRY_ST(ensure_lane_work(ctx, L, std::max(l1, l2)));
+    PR_BLAS(ctx, cusolverDnDgeqrf(L.sol, m, nc, A, m, L.tau, *L.work, (int)*L.work_len, L.info), "geqrf");
+    extract_r<<<blocks_for((int64_t)nc * nc), kT, 0, L.st>>>(A, Rout, m, nc);
+    PR_BLAS(ctx, cusolverDnDorgqr(L.sol, m, nc, nc, A, m, L.tau, *L.work, (int)*L.work_len, L.info), "orgqr");
     return PR_OK;
 }
 
@@ -635,23 +732,89 @@ int rank_cut_host(const std::vector<double>& sig, double tol) {
     return r;
 }
 
+// Singular values below this fraction of the largest are not resolved by the
+// eigenproblem of H^T H in FP64 (their squares sit at 1e-12 of the largest,
+// 1e4 ulps): svd_eig_ leaves such spectra to gesvd.
+constexpr double kEigFloor = 1e-6;
+
+// SVD of H (h x h) for FP32 contexts from the symmetric eigenproblem of
+// H^T H (cuSOLVER syevd, several times faster than gesvd at h ~ 500):
+// H^T H = V Lambda V^T gives Y_h = V (descending order) and sigma =
+// sqrt(lambda); X_h is the orthonormal factor of the QR of H V (columns in
+// descending order, signs making R's diagonal positive), which restores
+// orthogonality that the squared spectrum loses for the small sigma.  Fills
+// d->Xh, d->YhT (rows 0..r-1), d->sig and `sig`; *used = false (nothing
+// written) when a kept sigma lies below kEigFloor sigma_max.
+pr_status svd_eig_(pr_ctx* ctx, pr_driver* d, int h, double tol, std::vector<double>& sig, int& r, bool& used,
+                   cudaStream_t st) {
+    const double one = 1.0, zero = 0.0;
+    used = false;
+    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, h, h, h, &one, d->H, h, d->H, h, &zero, d->E, h), "H^T H");
+    int lw = 0;
+    PR_BLAS(ctx, cusolverDnDsyevd_bufferSize(d->sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, h, d->E, h,
+                                             d->sig, &lw), "syevd size");
+    PR_TRY_ST(ensure_work(ctx, d, lw));
+    PR_BLAS(ctx, cusolverDnDsyevd(d->sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, h, d->E, h, d->sig,
+                                  d->work, (int)d->work_len, d->info), "syevd");
+    std::vector<double> lam(h);
+    int info = 0;
+    cudaMemcpyAsync(lam.data(), d->sig, (size_t)h * 8, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&info, d->info, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "syevd");
+    if (info != 0) return PR_OK;   // not converged: gesvd instead
+    sig.assign(h, 0.0);
+    for (int i = 0; i < h; ++i) sig[i] = std::sqrt(std::max(lam[h - 1 - i], 0.0));
+    r = rank_cut_host(sig, tol);
+    if (r > 0 && sig[r - 1] < kEigFloor * sig[0]) return PR_OK;
+    used = true;
+    if (r == 0) return PR_OK;
+    // V (descending, r columns) into Xh, then YhT = V^T
+    reverse_cols<<<blocks_for((int64_t)h * r), kT, 0, st>>>(d->E, d->Xh, h, r);
+    PR_BLAS(ctx, cublasDgeam(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, r, h, &one, d->Xh, h, &zero, d->Xh, r, d->YhT, h),
+            "V^T");
+    // X_h = orthonormal factor of H V (Householder QR, columns in the order
+    // of decreasing sigma, signs making R's diagonal positive)
+    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, h, r, h, &one, d->H, h, d->Xh, h, &zero, d->E, h), "H V");
+    int l1 = 0, l2 = 0;
+    PR_BLAS(ctx, cusolverDnDgeqrf_bufferSize(d->sol, h, r, d->E, h, &l1), "geqrf size");
+    PR_BLAS(ctx, cusolverDnDorgqr_bufferSize(d->sol, h, r, r, d->E, h, d->tauh, &l2), "orgqr size");
+    PR_TRY_ST(ensure_work(ctx, d, std::max(l1, l2)));
+    PR_BLAS(ctx, cusolverDnDgeqrf(d->sol, h, r, d->E, h, d->tauh, d->work, (int)d->work_len, d->info), "geqrf");
+    diag_sign<<<blocks_for(r), kT, 0, st>>>(d->E, h, r, d->rsign);
+    PR_BLAS(ctx, cusolverDnDorgqr(d->sol, h, r, r, d->E, h, d->tauh, d->work, (int)d->work_len, d->info), "orgqr");
+    scale_cols<<<blocks_for((int64_t)h * r), kT, 0, st>>>(d->E, d->rsign, d->Xh, h, r);
+    cudaMemcpyAsync(d->sig, sig.data(), (size_t)h * 8, cudaMemcpyHostToDevice, st);
+    e = cudaStreamSynchronize(st);   // `sig` is a host vector the copy reads
+    if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "svd_eig");
+    return PR_OK;
+}
+
 // C (rows x nc) = B^T A with B = Bb W (Bb rows x hb, W hb x s, ld bcap): C is
 // s x nc, through T = Bb^T A (hb x nc)
-pr_status project_(pr_ctx* ctx, pr_driver* d, const double* Bb, const double* W, const double* A, int nc,
-                   double* C) {
+pr_status project_(pr_ctx* ctx, pr_driver* d, const Lane& L, const double* Bb, const double* W, const double* A,
+                   int nc, double* C) {
     const double one = 1.0, zero = 0.0;
     const int64_t rows = d->rows;
-    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, d->hb, nc, (int)rows, &one, Bb, (int)rows, A, (int)rows, &zero, d->Tb, d->hb), "Bb^T A");
-    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, d->s, nc, d->hb, &one, W, d->bcap, d->Tb, d->hb, &zero, C, d->s), "W^T T");
+    if (d->tc) {
+        PR_TRY_ST(tc_gram_launch(Bb, rows, A, rows, rows, d->hb, nc, L.Tb, d->hb, ctx->dev_flag, L.st));
+    } else {
+        PR_BLAS(ctx, cublasDgemm(L.blas, CUBLAS_OP_T, CUBLAS_OP_N, d->hb, nc, (int)rows, &one, Bb, (int)rows, A, (int)rows, &zero, L.Tb, d->hb), "Bb^T A");
+    }
+    PR_BLAS(ctx, cublasDgemm(L.blas, CUBLAS_OP_T, CUBLAS_OP_N, d->s, nc, d->hb, &one, W, d->bcap, L.Tb, d->hb, &zero, C, d->s), "W^T T");
     return PR_OK;
 }
 // A -= (Bb W) C for C (s x nc), through T = W C (hb x nc)
-pr_status subtract_(pr_ctx* ctx, pr_driver* d, const double* Bb, const double* W, const double* C, int nc,
-                    double* A) {
+pr_status subtract_(pr_ctx* ctx, pr_driver* d, const Lane& L, const double* Bb, const double* W, const double* C,
+                    int nc, double* A) {
     const double one = 1.0, zero = 0.0, mone = -1.0;
     const int64_t rows = d->rows;
-    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, d->hb, nc, d->s, &one, W, d->bcap, C, d->s, &zero, d->Tb, d->hb), "W C");
-    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, nc, d->hb, &mone, Bb, (int)rows, d->Tb, d->hb, &one, A, (int)rows), "A - Bb T");
+    PR_BLAS(ctx, cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, d->hb, nc, d->s, &one, W, d->bcap, C, d->s, &zero, L.Tb, d->hb), "W C");
+    if (d->tc) {
+        PR_TRY_ST(tc_update_launch(Bb, rows, L.Tb, d->hb, A, rows, rows, d->hb, nc, A, rows, ctx->dev_flag, L.st));
+    } else {
+        PR_BLAS(ctx, cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, nc, d->hb, &mone, Bb, (int)rows, L.Tb, d->hb, &one, A, (int)rows), "A - Bb T");
+    }
     return PR_OK;
 }
 
@@ -665,17 +828,37 @@ pr_status update_svd(pr_ctx* ctx, pr_driver* d, double* F, double* G, int nc, cu
     const double one = 1.0, zero = 0.0;
     PR_TRY_ST(ensure_capacity(ctx, d, s + nc, nc, st));
     const int h = s + nc;
+    cudaEventRecord(d->cev[0], st);
+    // F's steps on lane f (the caller's stream), G's on lane g, joined below
+    const Lane lf = lane_f(d, st), lg = lane_g(d);
+    cudaEventRecord(d->ev_fork, st);
+    cudaStreamWaitEvent(d->st2, d->ev_fork, 0);
     if (s > 0) {
         // U_F = U^T F, V_G = V^T G, then F - U U_F, G - V V_G
-        PR_TRY_ST(project_(ctx, d, d->Xb, d->WX, F, nc, d->UF));
-        PR_TRY_ST(project_(ctx, d, d->Yb, d->WY, G, nc, d->VG));
-        PR_TRY_ST(subtract_(ctx, d, d->Xb, d->WX, d->UF, nc, F));
-        PR_TRY_ST(subtract_(ctx, d, d->Yb, d->WY, d->VG, nc, G));
+        PR_TRY_ST(project_(ctx, d, lf, d->Xb, d->WX, F, nc, d->UF));
+        PR_TRY_ST(project_(ctx, d, lg, d->Yb, d->WY, G, nc, d->VG));
+        PR_TRY_ST(subtract_(ctx, d, lf, d->Xb, d->WX, d->UF, nc, F));
+        PR_TRY_ST(subtract_(ctx, d, lg, d->Yb, d->WY, d->VG, nc, G));
+        if (d->tc) {
+            // FP32-level products: project and deflate once more (classical
+            // Gram-Schmidt twice), so that Q_F, Q_G stay orthogonal to the
+            // bases to working accuracy when F, G lie nearly in their span
+            PR_TRY_ST(project_(ctx, d, lf, d->Xb, d->WX, F, nc, d->A1));
+            PR_TRY_ST(project_(ctx, d, lg, d->Yb, d->WY, G, nc, d->A2));
+            PR_TRY_ST(subtract_(ctx, d, lf, d->Xb, d->WX, d->A1, nc, F));
+            PR_TRY_ST(subtract_(ctx, d, lg, d->Yb, d->WY, d->A2, nc, G));
+            PR_BLAS(ctx, cublasDaxpy(lf.blas, s * nc, &one, d->A1, 1, d->UF, 1), "UF += dUF");
+            PR_BLAS(ctx, cublasDaxpy(lg.blas, s * nc, &one, d->A2, 1, d->VG, 1), "VG += dVG");
+        }
     }
+    cudaEventRecord(d->cev[1], st);
     cudaMemcpyAsync(d->QF, F, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(d->QG, G, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
-    PR_TRY_ST(qr_(ctx, d, d->QF, d->RF, nc, st));
-    PR_TRY_ST(qr_(ctx, d, d->QG, d->RG, nc, st));
+    cudaMemcpyAsync(d->QG, G, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, d->st2);
+    PR_TRY_ST(qr_(ctx, d, lf, d->QF, d->RF, nc));
+    PR_TRY_ST(qr_(ctx, d, lg, d->QG, d->RG, nc));
+    cudaEventRecord(d->ev_join, d->st2);
+    cudaStreamWaitEvent(st, d->ev_join, 0);
+    cudaEventRecord(d->cev[2], st);
     // A1 = [U_F; R_F], A2 = [V_G; R_G]  (h x nc), H = A1 A2^T + diag(S, 0)
     if (s > 0) {
         copy_block<<<blocks_for((int64_t)s * nc), kT, 0, st>>>(d->UF, s, d->A1, h, s, nc, 0);
@@ -685,13 +868,22 @@ pr_status update_svd(pr_ctx* ctx, pr_driver* d, double* F, double* G, int nc, cu
     copy_block<<<blocks_for((int64_t)nc * nc), kT, 0, st>>>(d->RG, nc, d->A2, h, nc, nc, s);
     PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_T, h, h, nc, &one, d->A1, h, d->A2, h, &zero, d->H, h), "H");
     if (s > 0) add_diag<<<1, kT, 0, st>>>(d->H, h, d->S, s);
-    PR_TRY_ST(svd_(ctx, d, h, st));
     std::vector<double> sig(h);
-    cudaMemcpy(sig.data(), d->sig, (size_t)h * 8, cudaMemcpyDeviceToHost);
-    const int r = rank_cut_host(sig, ctx->opts.tol);
+    int r = 0;
+    bool eig_used = false;
+    if (d->tc) PR_TRY_ST(svd_eig_(ctx, d, h, ctx->opts.tol, sig, r, eig_used, st));
+    if (!eig_used) {
+        PR_TRY_ST(svd_(ctx, d, h, st));
+        cudaMemcpy(sig.data(), d->sig, (size_t)h * 8, cudaMemcpyDeviceToHost);
+        r = rank_cut_host(sig, ctx->opts.tol);
+    }
+    d->eig_svds += eig_used ? 1 : 0;
+    d->all_svds += 1;
+    cudaEventRecord(d->cev[3], st);
     if (r == 0) {
         d->s = 0;
         d->hb = 0;
+        cudaEventRecord(d->cev[4], st);
         return PR_OK;
     }
     // U~ = [U Q_F] X_h(:, 1:r), V~ = [V Q_G] Y_h(:, 1:r)   (Y_h = YhT^T):
@@ -708,6 +900,7 @@ pr_status update_svd(pr_ctx* ctx, pr_driver* d, double* F, double* G, int nc, cu
     std::swap(d->WX, d->WXn);
     std::swap(d->WY, d->WYn);
     cudaMemcpyAsync(d->S, d->sig, (size_t)r * 8, cudaMemcpyDeviceToDevice, st);
+    cudaEventRecord(d->cev[4], st);
     d->s = r;
     d->hb = hb + nc;
     return PR_OK;
@@ -739,8 +932,8 @@ pr_status residual_(pr_ctx* ctx, pr_driver* d, const double* F, const double* G,
     // QF (rows x nc) <- F - X (Y^T G): reuse QF/UF scratch (UF has >= s*nc)
     cudaMemcpyAsync(d->QF, F, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
     if (d->s > 0) {
-        PR_TRY_ST(project_(ctx, d, d->Yb, d->WY, G, nc, d->UF));
-        PR_TRY_ST(subtract_(ctx, d, d->Xb, d->WX, d->UF, nc, d->QF));
+        PR_TRY_ST(project_(ctx, d, lane_f(d, st), d->Yb, d->WY, G, nc, d->UF));
+        PR_TRY_ST(subtract_(ctx, d, lane_f(d, st), d->Xb, d->WX, d->UF, nc, d->QF));
     }
     PR_BLAS(ctx, cublasDnrm2(d->blas, (int)(rows * nc), d->QF, 1, &nr), "nrm2");
     *res = nf > 0 ? nr / nf : 0.0;
@@ -806,16 +999,43 @@ extern "C" pr_status pr_procrustes_reset(pr_ctx* ctx) {
     return PR_OK;
 }
 
+namespace {
+
+// What the reverse sweep of pr_iterate_adjoint needs from the forward run:
+// every iteration's states and its frozen corrector Omega^k = X_k Y_k^T, kept
+// as (hb_k, s_k) and copies of W_X, W_Y (X_b, Y_b only grow, so their first
+// hb_k columns are still those of iteration k).
+struct IterRecord {
+    char* hu = nullptr;            // [(K+1)][N+1][pts] dtype: u^k_n at hu + ((k-1)(N+1) + n) pts
+    char* hv = nullptr;
+    std::vector<int> hb, s;        // per iteration k = 1..K
+    std::vector<double*> wx, wy;   // hb_k x s_k, column-major (ld hb_k)
+};
+
+pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector, double tol_err,
+                      const void* u_ref, const void* v_ref, void* u_slices, void* v_slices, double* err_hist,
+                      double* resid_hist, int* rank_hist, int* k_done, cudaStream_t st, IterRecord* rec);
+
+}  // namespace
+
 extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector,
                                 double tol_err, const void* u_ref, const void* v_ref, void* u_slices,
                                 void* v_slices, double* err_hist, double* resid_hist, int* rank_hist,
                                 int* k_done, void* stream) {
+    return iterate_run(ctx, u0, p0, K, corrector, tol_err, u_ref, v_ref, u_slices, v_slices, err_hist, resid_hist,
+                       rank_hist, k_done, (cudaStream_t)stream, nullptr);
+}
+
+namespace {
+
+pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector, double tol_err,
+                      const void* u_ref, const void* v_ref, void* u_slices, void* v_slices, double* err_hist,
+                      double* resid_hist, int* rank_hist, int* k_done, cudaStream_t st, IterRecord* rec) {
     if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_iterate: ctx is NULL");
     if (!u0 || !p0 || !u_slices || !v_slices) return pr_fail(ctx, PR_EINVAL, "pr_iterate: NULL array");
     if (K < 0) return pr_fail(ctx, PR_EINVAL, "pr_iterate: K must be >= 0");
     if (corrector < PR_CORR_PROCRUSTES || corrector > PR_CORR_PLAIN)
         return pr_fail(ctx, PR_EINVAL, "pr_iterate: unknown corrector");
-    cudaStream_t st = (cudaStream_t)stream;
     pr_driver* d = nullptr;
     PR_TRY_ST(driver(ctx, st, &d));
     d->s = 0;   // a new run starts with an empty correlation matrix (Alg. 3)
@@ -824,6 +1044,8 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
         d->phase_ms[i] = 0.0;
         if (!d->ev[i]) PR_CUDA_TRY(ctx, cudaEventCreate(&d->ev[i]));
     }
+    for (int i = 0; i < 5; ++i) d->corr_ms[i] = 0.0;
+    d->eig_svds = d->all_svds = 0;
     // elapsed time between two recorded events, added to a phase total
     auto add_phase = [&](int ph, int a, int b) -> pr_status {
         float ms = 0.0f;
@@ -856,6 +1078,14 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
     }
     cudaEventRecord(d->ev[1], st);
     PR_TRY_ST(add_phase(0, 0, 1));
+    // the forward record: states of iteration k (k = 1: the initial guess)
+    auto record_states = [&](int k) {
+        if (!rec) return;
+        const size_t b = (size_t)(N + 1) * pts * esz, o = (size_t)(k - 1) * b;
+        cudaMemcpyAsync(rec->hu + o, us, b, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(rec->hv + o, vs, b, cudaMemcpyDeviceToDevice, st);
+    };
+    record_states(1);
     for (int k = 1; k <= K; ++k) {
         // parallel phase: v_n = F u^k_{n-1}, U_n = C R u^k_{n-1}, n = 1..N
         cudaEventRecord(d->ev[0], st);
@@ -877,6 +1107,33 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
             cudaMemcpyAsync(d->G2, d->Gm, (size_t)d->rows * N * 8, cudaMemcpyDeviceToDevice, st);
             PR_TRY_ST(update_svd(ctx, d, d->Fm, d->Gm, N, st));
             PR_TRY_ST(residual_(ctx, d, d->F2, d->G2, N, &res, st));
+            cudaEventRecord(d->cev[5], st);
+            {
+                PR_CUDA_TRY(ctx, cudaEventSynchronize(d->cev[5]));
+                for (int i = 0; i < 5; ++i) {
+                    float ms = 0.0f;
+                    PR_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, d->cev[i], d->cev[i + 1]));
+                    d->corr_ms[i] += ms;
+                }
+            }
+            if (rec) {
+                // freeze Omega^k: the W blocks (hb x s, ld bcap) as they are now
+                double* wx = nullptr;
+                double* wy = nullptr;
+                const size_t wb = (size_t)std::max(1, d->hb) * std::max(1, d->s) * 8;
+                PR_TRY_ST(alloc(ctx, (void**)&wx, wb, "pr_iterate_adjoint: record"));
+                rec->wx.push_back(wx);
+                PR_TRY_ST(alloc(ctx, (void**)&wy, wb, "pr_iterate_adjoint: record"));
+                rec->wy.push_back(wy);
+                rec->hb.push_back(d->hb);
+                rec->s.push_back(d->s);
+                if (d->s > 0) {
+                    cudaMemcpy2DAsync(wx, (size_t)d->hb * 8, d->WX, (size_t)d->bcap * 8, (size_t)d->hb * 8, d->s,
+                                      cudaMemcpyDeviceToDevice, st);
+                    cudaMemcpy2DAsync(wy, (size_t)d->hb * 8, d->WY, (size_t)d->bcap * 8, (size_t)d->hb * 8, d->s,
+                                      cudaMemcpyDeviceToDevice, st);
+                }
+            }
         }
         cudaEventRecord(d->ev[2], st);
         // serial corrected sweep; u^{k+1}_0 = u^k_0 stays
@@ -903,6 +1160,7 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
             PR_TRY_ST(interp_(ctx, d, (char*)d->vF_u + vo, (char*)d->vF_v + vo, fu(n), fv(n), st));
         }
         cudaEventRecord(d->ev[3], st);
+        record_states(k + 1);
         PR_TRY_ST(add_phase(1, 0, 1));
         PR_TRY_ST(add_phase(2, 1, 2));
         PR_TRY_ST(add_phase(3, 2, 3));
@@ -944,8 +1202,499 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
     return PR_OK;
 }
 
+}  // namespace
+
+extern "C" pr_status pr_iterate_corrector_phases(const pr_ctx* ctx, double* ms, int* eig_svds, int* svds) {
+    if (!ctx || !ms) return PR_EINVAL;
+    for (int i = 0; i < 5; ++i) ms[i] = ctx->drv ? ctx->drv->corr_ms[i] : 0.0;
+    if (eig_svds) *eig_svds = ctx->drv ? ctx->drv->eig_svds : 0;
+    if (svds) *svds = ctx->drv ? ctx->drv->all_svds : 0;
+    return PR_OK;
+}
+
 extern "C" pr_status pr_iterate_phases(const pr_ctx* ctx, double* ms) {
     if (!ctx || !ms) return PR_EINVAL;
     for (int i = 0; i < 4; ++i) ms[i] = ctx->drv ? ctx->drv->phase_ms[i] : 0.0;
     return PR_OK;
+}
+
+// ============================================================================
+// Adjoint of the parareal solve with the correctors frozen (pr_iterate_adjoint)
+//
+// The paper does not differentiate its method.  Every iteration's corrector
+// Omega^k = X_k Y_k^T is held at the value the forward run computed (Alg. 1
+// on its data), so the map (u0, p0, c) -> u^{K+1}_N is a composition of F, C
+// (Sec. 3.1), R, I (Sec. 6), Lambda, Lambda^dagger (Sec. 3.4, Alg. 2) and
+// fixed matrices.  The reverse sweep applies their transposes in reverse
+// order:
+//   R^T     scatter onto the coarse nodes of a zero fine field;
+//   I^T     with I = Re(G_f^* P G_c) (G the unnormalised DFT, P the padding
+//           with the Nyquist split and the 1/N_Dx scale): Re(G_c P^T G_f^* y);
+//   Lambda^T [q; p] = [-sum_a D_a q_a ; p / c], D_a the central difference;
+//   Lambda^dagger^T: q_a = Re(G D_a G^* w) / N_Dx with D_a = -i xi_a / |xi|^2,
+//           zero mode sum(w) / N_Dx, p = c w_t;
+//   Omega^T = Y X^T;  F^T, C^T the transposed level recurrence (adjoint.cu).
+// dL/dc collects the fine kappa term, the coarse kappa term and the c
+// dependence of Lambda (c^-1 w_t) and Lambda^dagger (c p), the coarse terms
+// scattered back by R^T (the coarse c is R c).
+// ============================================================================
+namespace {
+
+template <typename S, typename D, int DIM>
+__global__ void restrict_T_add(const S* __restrict__ a, const S* __restrict__ b, D* __restrict__ fa,
+                               D* __restrict__ fb, int64_t n, int ratio, int64_t cpts) {
+    const int64_t nc = n / ratio;
+    for (int64_t J = (int64_t)blockIdx.x * kT + threadIdx.x; J < cpts; J += (int64_t)gridDim.x * kT) {
+        int64_t c[3];
+        coords<DIM>(J, nc, c);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) c[q] *= ratio;
+        const int64_t f = lin<DIM>(c, n);
+        fa[f] = (D)((double)fa[f] + (double)a[J]);
+        if (b) fb[f] = (D)((double)fb[f] + (double)b[J]);
+    }
+}
+
+template <typename T>
+__global__ void fine_pair_to_complex(const T* __restrict__ a, const T* __restrict__ b,
+                                     cufftDoubleComplex* __restrict__ z, int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
+        z[j] = make_cuDoubleComplex((double)a[j], 0.0);
+        z[m + j] = make_cuDoubleComplex((double)b[j], 0.0);
+    }
+}
+
+// P^T of interp_pad: coarse coefficient (fld, J) = sum over the fine indices
+// that interp_pad fills from it, with the same weights (1/cpts included)
+template <int DIM>
+__global__ void interp_pad_T(const cufftDoubleComplex* __restrict__ fs, cufftDoubleComplex* __restrict__ cs,
+                             int64_t nc, int64_t nf, int64_t cpts, int64_t fpts) {
+    const double scale = 1.0 / (double)cpts;
+    const int64_t half = nc / 2;
+    for (int64_t idx = (int64_t)blockIdx.x * kT + threadIdx.x; idx < 2 * cpts; idx += (int64_t)gridDim.x * kT) {
+        const int64_t fld = idx / cpts, J = idx - fld * cpts;
+        int64_t c[3];
+        coords<DIM>(J, nc, c);
+        // per axis: up to two fine indices with their weights
+        int64_t fi[3][2];
+        double fw[3][2];
+        int cnt[3];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int64_t j = c[a];
+            cnt[a] = 1;
+            fw[a][0] = 1.0;
+            fw[a][1] = 0.0;
+            fi[a][1] = 0;
+            if (nc % 2 == 0) {
+                if (j < half) fi[a][0] = j;
+                else if (j > half) fi[a][0] = j - nc + nf;
+                else {
+                    fi[a][0] = half;
+                    fw[a][0] = 0.5;
+                    fi[a][1] = nf - half;
+                    fw[a][1] = 0.5;
+                    cnt[a] = 2;
+                }
+            } else {
+                fi[a][0] = j <= half ? j : j - nc + nf;
+            }
+        }
+        double re = 0.0, im = 0.0;
+        const int combos = 1 << DIM;
+        for (int m = 0; m < combos; ++m) {
+            double w = scale;
+            int64_t f[3];
+            bool ok = true;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const int bit = (m >> a) & 1;
+                if (bit >= cnt[a]) ok = false;
+                f[a] = fi[a][bit];
+                w *= fw[a][bit];
+            }
+            if (!ok) continue;
+            const cufftDoubleComplex x = fs[fld * fpts + lin<DIM>(f, nf)];
+            re += w * x.x;
+            im += w * x.y;
+        }
+        cs[idx] = make_cuDoubleComplex(re, im);
+    }
+}
+
+__global__ void complex_real_pair(const cufftDoubleComplex* __restrict__ z, double* __restrict__ a,
+                                  double* __restrict__ b, int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
+        a[j] = z[j].x;
+        b[j] = z[m + j].x;
+    }
+}
+
+// Z[a][J] = D_a(J) B[J], D_a = -i xi_a / |xi|^2 (0 at xi = 0), a < DIM
+template <int DIM>
+__global__ void grad2func_T_spread(const cufftDoubleComplex* __restrict__ B, cufftDoubleComplex* __restrict__ Z,
+                                   int64_t nc, int64_t cpts) {
+    for (int64_t J = (int64_t)blockIdx.x * kT + threadIdx.x; J < cpts; J += (int64_t)gridDim.x * kT) {
+        int64_t c[3];
+        coords<DIM>(J, nc, c);
+        double xi[3], mag2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            xi[a] = 2.0 * M_PI * (double)freq(c[a], nc);
+            mag2 += xi[a] * xi[a];
+        }
+        const cufftDoubleComplex b = B[J];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            // (-i xi / m)(x + i y) = xi y / m - i xi x / m
+            Z[a * cpts + J] = mag2 > 0 ? make_cuDoubleComplex(xi[a] * b.y / mag2, -xi[a] * b.x / mag2)
+                                       : make_cuDoubleComplex(0.0, 0.0);
+        }
+    }
+}
+
+// q[a*cpts + J] = Re(Z[a][J]) / cpts, the vector part of Lambda^dagger^T;
+// q[DIM*cpts + J] = c_J bdut_J; bcc_J += bdut_J p_J (the c in u_t = c p)
+template <int DIM>
+__global__ void grad2func_T_finish(const cufftDoubleComplex* __restrict__ Z, const double* __restrict__ bdut,
+                                   const double* __restrict__ cc, const double* __restrict__ pvec,
+                                   double* __restrict__ q, double* __restrict__ bcc, int64_t cpts) {
+    const double inv = 1.0 / (double)cpts;
+    for (int64_t J = (int64_t)blockIdx.x * kT + threadIdx.x; J < cpts; J += (int64_t)gridDim.x * kT) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) q[a * cpts + J] = Z[a * cpts + J].x * inv;
+        q[DIM * cpts + J] = cc[J] * bdut[J];
+        bcc[J] += bdut[J] * pvec[J];
+    }
+}
+
+// sum_J x_J / cpts into *out (one block, fixed order)
+__global__ void mean_kernel(const double* __restrict__ x, int64_t cpts, double* __restrict__ out) {
+    __shared__ double red[1024];
+    double acc = 0.0;
+    for (int64_t j = threadIdx.x; j < cpts; j += blockDim.x) acc += x[j];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] / (double)cpts;
+}
+
+// Lambda^T of q (rows = (DIM+1) cpts) for the difference Lambda w - Lambda U:
+// bw = -sum_a D_a q_a + z, bwt = p / c, written to (bw, bwt) of w (dtype T)
+// and subtracted from (bU, bUt) of U; bcc -= p (wt - Ut) / c^2.
+template <typename T, int DIM>
+__global__ void lambda_T_diff(const double* __restrict__ q, const double* __restrict__ cc, const T* __restrict__ wt,
+                              const T* __restrict__ Ut, const double* __restrict__ zmode, T* __restrict__ bw,
+                              T* __restrict__ bwt, T* __restrict__ bU, T* __restrict__ bUt, double* __restrict__ bcc,
+                              int64_t nc, int64_t cpts, int order_half, Beta beta, double inv_dx) {
+    for (int64_t J = (int64_t)blockIdx.x * kT + threadIdx.x; J < cpts; J += (int64_t)gridDim.x * kT) {
+        int64_t c[3];
+        coords<DIM>(J, nc, c);
+        double g = 0.0;
+        int64_t astride = 1;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const double* qa = q + a * cpts;
+            for (int k = 1; k <= order_half; ++k) {
+                const int64_t cp = (c[a] + k) % nc, cm = (c[a] - k + nc) % nc;
+                const double qp = qa[J + (cp - c[a]) * astride], qm = qa[J + (cm - c[a]) * astride];
+                g += beta.b[k - 1] * (qm - qp);
+            }
+            astride *= nc;
+        }
+        const double vw = g * inv_dx + *zmode;
+        const double p = q[DIM * cpts + J];
+        const double vt = p / cc[J];
+        bw[J] = (T)vw;
+        bwt[J] = (T)vt;
+        bU[J] = (T)((double)bU[J] - vw);
+        bUt[J] = (T)((double)bUt[J] - vt);
+        bcc[J] -= p * ((double)wt[J] - (double)Ut[J]) / (cc[J] * cc[J]);
+    }
+}
+
+template <typename T>
+__global__ void axpy_kernel(T* __restrict__ y, const T* __restrict__ x, double a, int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT)
+        y[j] = (T)((double)y[j] + a * (double)x[j]);
+}
+
+template <typename T>
+__global__ void from_double_kernel(T* __restrict__ y, const double* __restrict__ x, int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) y[j] = (T)x[j];
+}
+
+// gc_J (fine, FP64) = gk_J * 2 c_J scale
+__global__ void kappa_to_c(const double* __restrict__ gk, const double* __restrict__ c, double* __restrict__ gc,
+                           int64_t m, double scale, int accumulate) {
+    for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT)
+        gc[j] = (accumulate ? gc[j] : 0.0) + gk[j] * 2.0 * c[j] * scale;
+}
+
+template <typename T>
+struct AdjWork {
+    T *bu = nullptr, *bv = nullptr;      // [N+1][pts] adjoints of u^{k+1}_n
+    T *nu = nullptr, *nv = nullptr;      // [N+1][pts] adjoints of u^k_n (being formed)
+    T *fvu = nullptr, *fvv = nullptr;    // [N][pts] adjoints of v_n = F u^k_{n-1}
+    T *cU = nullptr, *cV = nullptr;      // [N][cpts] adjoints of U_n = C R u^k_{n-1}
+    T *iu = nullptr, *iv = nullptr;      // [pts] adjoint of u^1_0 gathered from every u^{k+1}_0
+    T *wu = nullptr, *wv = nullptr;      // [cpts] adjoint of w = C R u^{k+1}_{n-1}
+    T *Ru = nullptr, *Rv = nullptr;      // [cpts] R of a fine state
+    T *tu = nullptr, *tv = nullptr;      // [cpts] scratch
+    double *gkf = nullptr, *gkc = nullptr, *bcc = nullptr;   // dL/dkappa fine, coarse; Lambda c terms
+    double *bdu = nullptr, *bdut = nullptr, *q = nullptr, *zm = nullptr, *gcf = nullptr;
+    std::vector<void*> all;
+};
+
+template <typename T>
+pr_status adj_alloc(pr_ctx* ctx, AdjWork<T>& w, int64_t N, int64_t pts, int64_t cpts, int64_t rows) {
+    auto get = [&](auto** p, size_t bytes) -> pr_status {
+        void* q = nullptr;
+        PR_TRY_ST(alloc(ctx, &q, bytes, "pr_iterate_adjoint: workspace"));
+        cudaMemset(q, 0, bytes);
+        w.all.push_back(q);
+        *p = (std::remove_reference_t<decltype(*p)>)q;
+        return PR_OK;
+    };
+    const size_t e = sizeof(T);
+    PR_TRY_ST(get(&w.bu, (N + 1) * pts * e)); PR_TRY_ST(get(&w.bv, (N + 1) * pts * e));
+    PR_TRY_ST(get(&w.nu, (N + 1) * pts * e)); PR_TRY_ST(get(&w.nv, (N + 1) * pts * e));
+    PR_TRY_ST(get(&w.fvu, N * pts * e)); PR_TRY_ST(get(&w.fvv, N * pts * e));
+    PR_TRY_ST(get(&w.cU, N * cpts * e)); PR_TRY_ST(get(&w.cV, N * cpts * e));
+    PR_TRY_ST(get(&w.iu, pts * e)); PR_TRY_ST(get(&w.iv, pts * e));
+    PR_TRY_ST(get(&w.wu, cpts * e)); PR_TRY_ST(get(&w.wv, cpts * e));
+    PR_TRY_ST(get(&w.Ru, cpts * e)); PR_TRY_ST(get(&w.Rv, cpts * e));
+    PR_TRY_ST(get(&w.tu, cpts * e)); PR_TRY_ST(get(&w.tv, cpts * e));
+    PR_TRY_ST(get(&w.gkf, pts * 8)); PR_TRY_ST(get(&w.gkc, cpts * 8)); PR_TRY_ST(get(&w.bcc, cpts * 8));
+    PR_TRY_ST(get(&w.bdu, cpts * 8)); PR_TRY_ST(get(&w.bdut, cpts * 8)); PR_TRY_ST(get(&w.q, rows * 8));
+    PR_TRY_ST(get(&w.zm, 8)); PR_TRY_ST(get(&w.gcf, pts * 8));
+    return PR_OK;
+}
+
+// Omega^k g or (Omega^k)^T g with the frozen W blocks of iteration k
+pr_status apply_frozen(pr_ctx* ctx, pr_driver* d, const IterRecord& rec, int k, bool transpose, const double* g,
+                       double* out, cudaStream_t st) {
+    const int hb = rec.hb[k - 1], s = rec.s[k - 1];
+    if (s == 0) {
+        cudaMemsetAsync(out, 0, (size_t)d->rows * 8, st);
+        return PR_OK;
+    }
+    const double one = 1.0, zero = 0.0;
+    double* t1 = d->vb;
+    double* t2 = d->vb + d->bcap;
+    const double* Bin = transpose ? d->Xb : d->Yb;    // Omega = Xb WX WY^T Yb^T; Omega^T = Yb WY WX^T Xb^T
+    const double* Bout = transpose ? d->Yb : d->Xb;
+    const double* Win = transpose ? rec.wx[k - 1] : rec.wy[k - 1];
+    const double* Wout = transpose ? rec.wy[k - 1] : rec.wx[k - 1];
+    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_T, (int)d->rows, hb, &one, Bin, (int)d->rows, g, 1, &zero, t1, 1), "frozen Omega: B^T g");
+    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_T, hb, s, &one, Win, hb, t1, 1, &zero, d->rwork, 1), "frozen Omega: W^T");
+    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_N, hb, s, &one, Wout, hb, d->rwork, 1, &zero, t2, 1), "frozen Omega: W");
+    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_N, (int)d->rows, hb, &one, Bout, (int)d->rows, t2, 1, &zero, out, 1), "frozen Omega: B");
+    return PR_OK;
+}
+
+template <typename T, int DIM>
+pr_status adjoint_run(pr_ctx* ctx, pr_driver* d, const IterRecord& rec, int K, int corrector, const T* guT,
+                      const T* gvT, T* gc, T* gu0, T* gp0, cudaStream_t st) {
+    const int64_t pts = ctx->pts, cpts = d->cpts, nc = d->nc, n = ctx->n;
+    const int N = ctx->N;
+    pr_ctx* cc = ctx->coarse;
+    AdjWork<T> w;
+    pr_status status = adj_alloc<T>(ctx, w, N, pts, cpts, d->rows);
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        for (void* p : w.all) cudaFree(p);
+    };
+    if (status != PR_OK) {
+        release();
+        return status;
+    }
+    auto fail = [&](pr_status s) {
+        release();
+        return s;
+    };
+#define PR_ADJ_TRY(x) do { pr_status s_ = (x); if (s_ != PR_OK) return fail(s_); } while (0)
+    auto hu = [&](int k, int nn) { return (const T*)(rec.hu + ((size_t)(k - 1) * (N + 1) + nn) * pts * sizeof(T)); };
+    auto hv = [&](int k, int nn) { return (const T*)(rec.hv + ((size_t)(k - 1) * (N + 1) + nn) * pts * sizeof(T)); };
+    auto F_ = [&](T* base, int nn) { return base + (size_t)nn * pts; };
+    auto C_ = [&](T* base, int nn) { return base + (size_t)nn * cpts; };
+    const int h = ctx->opts.grad_order / 2;
+    const double inv_dxc = 1.0 / cc->dx;
+    // R u (coarse dtype) of a fine state into (Ru, Rv)
+    auto R_of = [&](const T* u, const T* v) { return restrict_(ctx, u, v, w.Ru, w.Rv, 1, st); };
+    // (fa, fb) += R^T (a, b)
+    auto RT_add = [&](const T* a, const T* b, T* fa, T* fb) {
+        restrict_T_add<T, T, DIM><<<blocks_for(cpts), kT, 0, st>>>(a, b, fa, fb, n, ctx->ratio, cpts);
+    };
+    // (bdu, bdut) (coarse FP64) = I^T (y_u, y_v) (fine dtype)
+    auto IT = [&](const T* yu, const T* yv) -> pr_status {
+        fine_pair_to_complex<T><<<blocks_for(pts), kT, 0, st>>>(yu, yv, d->zf, pts);
+        PR_FFT(ctx, cufftExecZ2Z(d->plan_f2, d->zf, d->zf, CUFFT_INVERSE), "I^T fine inverse");
+        interp_pad_T<DIM><<<blocks_for(2 * cpts), kT, 0, st>>>(d->zf, d->zc, nc, n, cpts, pts);
+        PR_FFT(ctx, cufftExecZ2Z(d->plan_c2, d->zc, d->zc, CUFFT_FORWARD), "I^T coarse forward");
+        complex_real_pair<<<blocks_for(cpts), kT, 0, st>>>(d->zc, w.bdu, w.bdut, cpts);
+        return PR_OK;
+    };
+    // adjoint of w = C R (su, sv) with incoming (au, av) (coarse dtype, consumed):
+    // (fu, fv) += R^T C^T (au, av), gkc += dL/dkappa_c
+    auto CRT = [&](const T* su, const T* sv, T* au, T* av, T* fu, T* fv) -> pr_status {
+        PR_TRY_ST(R_of(su, sv));
+        PR_TRY_ST(pr_slice_adjoint(cc, w.Ru, w.Rv, au, av, w.gkc, st));
+        RT_add(au, av, fu, fv);
+        return PR_OK;
+    };
+    cudaMemcpyAsync(F_(w.bu, N), guT, pts * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(F_(w.bv, N), gvT, pts * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    for (int k = K; k >= 1; --k) {
+        cudaMemsetAsync(w.fvu, 0, (size_t)N * pts * sizeof(T), st);
+        cudaMemsetAsync(w.fvv, 0, (size_t)N * pts * sizeof(T), st);
+        cudaMemsetAsync(w.cU, 0, (size_t)N * cpts * sizeof(T), st);
+        cudaMemsetAsync(w.cV, 0, (size_t)N * cpts * sizeof(T), st);
+        // serial corrected sweep of iteration k, in reverse
+        for (int nn = N; nn >= 1; --nn) {
+            T* bsu = F_(w.bu, nn);
+            T* bsv = F_(w.bv, nn);
+            // u^{k+1}_n = v_n + I(du, dut)
+            axpy_kernel<T><<<blocks_for(pts), kT, 0, st>>>(F_(w.fvu, nn - 1), bsu, 1.0, pts);
+            axpy_kernel<T><<<blocks_for(pts), kT, 0, st>>>(F_(w.fvv, nn - 1), bsv, 1.0, pts);
+            PR_ADJ_TRY(IT(bsu, bsv));
+            // w = C R u^{k+1}_{n-1} and U_n = C R u^k_{n-1}, recomputed
+            PR_ADJ_TRY(coarse_of(ctx, hu(k + 1, nn - 1), hv(k + 1, nn - 1), d->w_u, d->w_v, 1, st));
+            PR_ADJ_TRY(coarse_of(ctx, hu(k, nn - 1), hv(k, nn - 1), w.tu, w.tv, 1, st));
+            T* bUu = C_(w.cU, nn - 1);
+            T* bUv = C_(w.cV, nn - 1);
+            if (corrector == PR_CORR_PLAIN) {
+                // du = w - U_n: the adjoint of w is (bdu, bdut), of U_n minus it
+                from_double_kernel<T><<<blocks_for(cpts), kT, 0, st>>>(w.wu, w.bdu, cpts);
+                from_double_kernel<T><<<blocks_for(cpts), kT, 0, st>>>(w.wv, w.bdut, cpts);
+                axpy_kernel<T><<<blocks_for(cpts), kT, 0, st>>>(bUu, w.wu, -1.0, cpts);
+                axpy_kernel<T><<<blocks_for(cpts), kT, 0, st>>>(bUv, w.wv, -1.0, cpts);
+            } else {
+                // forward quantities: d = Lambda w - Lambda U_n, g = Omega d (its p block feeds dL/dc)
+                lambda_(ctx, d->w_u, d->w_v, d->dvec, 1, d->nc, cpts, 1.0, 1, d->rows, st);
+                lambda_(ctx, w.tu, w.tv, d->dvec, 1, d->nc, cpts, -1.0, 1, d->rows, st);
+                const double* g = d->dvec;
+                if (corrector == PR_CORR_PROCRUSTES) {
+                    PR_ADJ_TRY(apply_frozen(ctx, d, rec, k, false, d->dvec, d->gvec, st));
+                    g = d->gvec;
+                }
+                // Lambda^dagger^T of (bdu, bdut) for the difference
+                real_to_complex<<<blocks_for(cpts), kT, 0, st>>>(w.bdu, d->zc, cpts);
+                PR_FFT(ctx, cufftExecZ2Z(d->plan_c1, d->zc, d->zc, CUFFT_INVERSE), "Lambda^dagger^T inverse");
+                grad2func_T_spread<DIM><<<blocks_for(cpts), kT, 0, st>>>(d->zc, d->zc + cpts, nc, cpts);
+                PR_FFT(ctx, cufftExecZ2Z(d->plan_cd, d->zc + cpts, d->zc + cpts, CUFFT_FORWARD), "Lambda^dagger^T forward");
+                grad2func_T_finish<DIM><<<blocks_for(cpts), kT, 0, st>>>(d->zc + cpts, w.bdut, cc->c64,
+                                                                          g + (int64_t)DIM * cpts, w.q, w.bcc, cpts);
+                mean_kernel<<<1, 1024, 0, st>>>(w.bdu, cpts, w.zm);
+                double* qv = w.q;
+                if (corrector == PR_CORR_PROCRUSTES) {
+                    PR_ADJ_TRY(apply_frozen(ctx, d, rec, k, true, w.q, d->gvec, st));
+                    qv = d->gvec;
+                }
+                lambda_T_diff<T, DIM><<<blocks_for(cpts), kT, 0, st>>>(qv, cc->c64, (const T*)d->w_v, w.tv, w.zm,
+                                                                      w.wu, w.wv, bUu, bUv, w.bcc, nc, cpts, h,
+                                                                      d->beta, inv_dxc);
+            }
+            // w = C R u^{k+1}_{n-1}
+            PR_ADJ_TRY(CRT(hu(k + 1, nn - 1), hv(k + 1, nn - 1), w.wu, w.wv, F_(w.bu, nn - 1), F_(w.bv, nn - 1)));
+        }
+        // u^{k+1}_0 = u^1_0
+        axpy_kernel<T><<<blocks_for(pts), kT, 0, st>>>(w.iu, F_(w.bu, 0), 1.0, pts);
+        axpy_kernel<T><<<blocks_for(pts), kT, 0, st>>>(w.iv, F_(w.bv, 0), 1.0, pts);
+        // parallel phase of iteration k: v_n = F u^k_{n-1}, U_n = C R u^k_{n-1}
+        cudaMemsetAsync(w.nu, 0, (size_t)(N + 1) * pts * sizeof(T), st);
+        cudaMemsetAsync(w.nv, 0, (size_t)(N + 1) * pts * sizeof(T), st);
+        for (int nn = 1; nn <= N; ++nn) {
+            PR_ADJ_TRY(pr_slice_adjoint(ctx, hu(k, nn - 1), hv(k, nn - 1), F_(w.fvu, nn - 1), F_(w.fvv, nn - 1),
+                                        w.gkf, st));
+            axpy_kernel<T><<<blocks_for(pts), kT, 0, st>>>(F_(w.nu, nn - 1), F_(w.fvu, nn - 1), 1.0, pts);
+            axpy_kernel<T><<<blocks_for(pts), kT, 0, st>>>(F_(w.nv, nn - 1), F_(w.fvv, nn - 1), 1.0, pts);
+            PR_ADJ_TRY(CRT(hu(k, nn - 1), hv(k, nn - 1), C_(w.cU, nn - 1), C_(w.cV, nn - 1), F_(w.nu, nn - 1),
+                           F_(w.nv, nn - 1)));
+        }
+        std::swap(w.bu, w.nu);
+        std::swap(w.bv, w.nv);
+    }
+    // the initial guess u^1_n = I C R u^1_{n-1}, in reverse
+    for (int nn = N; nn >= 1; --nn) {
+        PR_ADJ_TRY(IT(F_(w.bu, nn), F_(w.bv, nn)));
+        from_double_kernel<T><<<blocks_for(cpts), kT, 0, st>>>(w.wu, w.bdu, cpts);
+        from_double_kernel<T><<<blocks_for(cpts), kT, 0, st>>>(w.wv, w.bdut, cpts);
+        PR_ADJ_TRY(CRT(hu(1, nn - 1), hv(1, nn - 1), w.wu, w.wv, F_(w.bu, nn - 1), F_(w.bv, nn - 1)));
+    }
+    axpy_kernel<T><<<blocks_for(pts), kT, 0, st>>>(F_(w.bu, 0), w.iu, 1.0, pts);
+    axpy_kernel<T><<<blocks_for(pts), kT, 0, st>>>(F_(w.bv, 0), w.iv, 1.0, pts);
+    cudaMemcpyAsync(gu0, F_(w.bu, 0), pts * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(gp0, F_(w.bv, 0), pts * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    // dL/dc: fine kappa term, then R^T of the coarse kappa and Lambda terms
+    kappa_to_c<<<blocks_for(pts), kT, 0, st>>>(w.gkf, ctx->c64, w.gcf, pts, ctx->dt_f / (ctx->dx * ctx->dx), 0);
+    kappa_to_c<<<blocks_for(cpts), kT, 0, st>>>(w.gkc, cc->c64, w.bcc, cpts, cc->dt_f / (cc->dx * cc->dx), 1);
+    restrict_T_add<double, double, DIM><<<blocks_for(cpts), kT, 0, st>>>(w.bcc, nullptr, w.gcf, nullptr, n,
+                                                                         ctx->ratio, cpts);
+    from_double_kernel<T><<<blocks_for(pts), kT, 0, st>>>(gc, w.gcf, pts);
+    cudaError_t e = cudaGetLastError();
+    release();
+    if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "pr_iterate_adjoint");
+    return PR_OK;
+#undef PR_ADJ_TRY
+}
+
+}  // namespace
+
+extern "C" pr_status pr_iterate_adjoint(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector,
+                                        const void* gu_T, const void* gv_T, void* gc, void* gu0, void* gp0,
+                                        void* stream) {
+    if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_iterate_adjoint: ctx is NULL");
+    if (!u0 || !p0 || !gu_T || !gv_T || !gc || !gu0 || !gp0)
+        return pr_fail(ctx, PR_EINVAL, "pr_iterate_adjoint: NULL array");
+    if (K < 1) return pr_fail(ctx, PR_EINVAL, "pr_iterate_adjoint: K must be >= 1");
+    if (corrector < PR_CORR_PROCRUSTES || corrector > PR_CORR_PLAIN)
+        return pr_fail(ctx, PR_EINVAL, "pr_iterate_adjoint: unknown corrector");
+    if (!ctx->coarse) return pr_fail(ctx, PR_EINVAL, "pr_iterate_adjoint: no coarse grid");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t esz = ctx->dtype == PR_F32 ? 4 : 8;
+    const int N = ctx->N;
+    const size_t slab = (size_t)(N + 1) * ctx->pts * esz;
+    IterRecord rec;
+    void* us = nullptr;
+    void* vs = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        cudaFree(rec.hu);
+        cudaFree(rec.hv);
+        cudaFree(us);
+        cudaFree(vs);
+        for (double* p : rec.wx) cudaFree(p);
+        for (double* p : rec.wy) cudaFree(p);
+    };
+    pr_status s = PR_OK;
+    if (cudaMalloc((void**)&rec.hu, slab * (K + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&rec.hv, slab * (K + 1)) != cudaSuccess || cudaMalloc(&us, slab) != cudaSuccess ||
+        cudaMalloc(&vs, slab) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return pr_fail(ctx, PR_ENOMEM, "pr_iterate_adjoint: state history");
+    }
+    int kd = 0;
+    s = iterate_run(ctx, u0, p0, K, corrector, 0.0, nullptr, nullptr, us, vs, nullptr, nullptr, nullptr, &kd, st, &rec);
+    if (s == PR_OK && kd != K) s = pr_fail(ctx, PR_ECUDA, "pr_iterate_adjoint: forward run stopped early");
+    if (s == PR_OK) {
+        pr_driver* d = ctx->drv;
+        const bool f32 = ctx->dtype == PR_F32;
+        switch (ctx->dim) {
+            case 1: s = f32 ? adjoint_run<float, 1>(ctx, d, rec, K, corrector, (const float*)gu_T, (const float*)gv_T, (float*)gc, (float*)gu0, (float*)gp0, st)
+                            : adjoint_run<double, 1>(ctx, d, rec, K, corrector, (const double*)gu_T, (const double*)gv_T, (double*)gc, (double*)gu0, (double*)gp0, st); break;
+            case 2: s = f32 ? adjoint_run<float, 2>(ctx, d, rec, K, corrector, (const float*)gu_T, (const float*)gv_T, (float*)gc, (float*)gu0, (float*)gp0, st)
+                            : adjoint_run<double, 2>(ctx, d, rec, K, corrector, (const double*)gu_T, (const double*)gv_T, (double*)gc, (double*)gu0, (double*)gp0, st); break;
+            default: s = f32 ? adjoint_run<float, 3>(ctx, d, rec, K, corrector, (const float*)gu_T, (const float*)gv_T, (float*)gc, (float*)gu0, (float*)gp0, st)
+                             : adjoint_run<double, 3>(ctx, d, rec, K, corrector, (const double*)gu_T, (const double*)gv_T, (double*)gc, (double*)gu0, (double*)gp0, st); break;
+        }
+    }
+    if (s == PR_OK) s = pr_take_flag(ctx, ctx, st, "pr_iterate_adjoint (fine sweep)");
+    if (s == PR_OK && ctx->coarse) s = pr_take_flag(ctx->coarse, ctx, st, "pr_iterate_adjoint (coarse sweep)");
+    cleanup();
+    return s;
 }

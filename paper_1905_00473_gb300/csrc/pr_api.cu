@@ -37,6 +37,8 @@ static void free_all(pr_ctx* c) {
     cudaFree(c->c64);
     cudaFree(c->adj_ws);
     c->adj_ws = nullptr;
+    cudaFree(c->sadj_ws);
+    c->sadj_ws = nullptr;
     cudaFree(c->kappa);
     cudaFree(c->kappa_il);
     cudaFree(c->cinv2);
@@ -47,6 +49,7 @@ static void free_all(pr_ctx* c) {
     }
     cudaFree(c->partials);
     cudaFree(c->dev_flag);
+    cudaFree(c->sweep_ctr);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
 }
@@ -240,7 +243,7 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
     // 0 = the deepest fused depth the geometry has (8, else 4), else one step per pass
     int depth = o.block_depth;
     if (depth == 0) depth = pr_tb2d_supported(ctx, 8) ? 8 : 4;
-    ctx->block_depth = pr_tb2d_supported(ctx, depth) ? depth : 1;
+    ctx->block_depth = (pr_tb2d_supported(ctx, depth) || pr_tb3d_supported(ctx, depth)) ? depth : 1;
 
     std::vector<char> kap(pts * esz);
     std::vector<double> cinv2(pts);
@@ -281,7 +284,8 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
         return fail(e, "pr_create: upload c");
     const size_t state = (size_t)N * pts;
     // the fused 2D sweeps carry a bfloat16 residual, one-level sweeps a byte
-    ctx->resid_bytes = o.dtype != PR_F32 ? 0 : (pr_tb2d_supported(ctx, 8) || pr_tb2d_supported(ctx, 4)) ? 2 : 1;
+    ctx->resid_bytes = o.dtype != PR_F32 ? 0
+                       : (pr_tb2d_supported(ctx, 8) || pr_tb2d_supported(ctx, 4) || pr_tb3d_supported(ctx, 4)) ? 2 : 1;
     for (int h = 0; h < 2; ++h) {
         if ((e = cudaMalloc(&ctx->su[h], state * esz)) != cudaSuccess) return fail(e, "pr_create: alloc scratch u");
         if ((e = cudaMalloc(&ctx->sv[h], state * esz)) != cudaSuccess) return fail(e, "pr_create: alloc scratch v");
@@ -290,6 +294,8 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
     }
     if ((e = cudaMalloc((void**)&ctx->dev_flag, sizeof(int))) != cudaSuccess) return fail(e, "pr_create: alloc flag");
     if ((e = cudaMemset(ctx->dev_flag, 0, sizeof(int))) != cudaSuccess) return fail(e, "pr_create: clear flag");
+    if ((e = cudaMalloc((void**)&ctx->sweep_ctr, sizeof(unsigned int))) != cudaSuccess)
+        return fail(e, "pr_create: alloc sweep counter");
     *out = ctx;
     return PR_OK;
 }
@@ -359,6 +365,35 @@ extern "C" pr_status pr_fine_all_slices(pr_ctx* ctx, const void* u_in, const voi
         return ctx->dtype == PR_F32 ? (char*)ctx->sr[h] + (size_t)n_begin * ctx->pts * rsz : nullptr;
     };
     pr_status s = PR_OK;
+    if (ctx->dtype == PR_F32 && depth == 8 && pr_tb2d_sweep_supported(ctx, passes)) {
+        // every pass of the sweep in one persistent launch
+        pr_sweep sw;
+        sw.u_in = ui;
+        sw.v_in = vi;
+        sw.u_out = uo;
+        sw.v_out = vo;
+        for (int h = 0; h < 2; ++h) {
+            sw.su[h] = scr_u(h);
+            sw.sv[h] = scr_v(h);
+            sw.sr[h] = scr_r(h);
+        }
+        sw.nslices = ns;
+        sw.passes = passes;
+        sw.last_levels = levels_total - (passes - 1) * depth;
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (ctx->prof_on) {
+            ea = prof_event(ctx);
+            eb = prof_event(ctx);
+            if (ea && eb) cudaEventRecord(ea, st);
+        }
+        s = pr_launch_fine_tb2d_sweep(ctx, sw, st);
+        if (ctx->prof_on && ea && eb) {
+            cudaEventRecord(eb, st);
+            ctx->prof.push_back({2, ea, eb});
+        }
+        if (cur != ctx->device && cur >= 0) cudaSetDevice(cur);
+        return s;
+    }
     for (int p = 0; p < passes && s == PR_OK; ++p) {
         pr_pass ps;
         ps.nslices = ns;
@@ -404,6 +439,12 @@ extern "C" pr_status pr_set_fused_columns(pr_ctx* ctx, int columns) {
     if (columns != 0 && columns != 2 && columns != 4)
         return pr_fail(ctx, PR_EINVAL, "pr_set_fused_columns: columns must be 0, 2 or 4");
     ctx->tb_cols = columns;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_set_one_launch(pr_ctx* ctx, int on) {
+    if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_set_one_launch: ctx is NULL");
+    ctx->one_launch = on != 0;
     return PR_OK;
 }
 

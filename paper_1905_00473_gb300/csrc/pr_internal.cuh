@@ -43,6 +43,8 @@ struct pr_ctx {
     double* partials = nullptr;     // energy partial sums
     int64_t partials_len = 0;
     int* dev_flag = nullptr;        // device-side error flag (bounded waits)
+    unsigned int* sweep_ctr = nullptr;   // grid-barrier counter of the one-launch sweep
+    int one_launch = 1;             // run a supported sweep as one persistent launch
     std::string err;
     // pr_profile: event pairs around launches, by kernel kind
     bool prof_on = false;
@@ -177,5 +179,24 @@ pr_status pr_launch_fine_tb2d(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
 bool pr_tb2d_extra_level(const pr_ctx* ctx);
 // the same passes with two columns per thread (16 warps per SM at n = 1024)
 pr_status pr_launch_fine_tb2d_c2(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
+
+// A whole sweep of fused passes in one persistent (cooperative) launch, a
+// grid barrier between passes (fine_tb2d.cu): `passes` passes of 8 levels,
+// the last one of last_levels (<= 9); pass scratch ping-pongs through su/sv/sr.
+struct pr_sweep {
+    const void* u_in;
+    const void* v_in;
+    void* u_out;
+    void* v_out;
+    void* su[2];
+    void* sv[2];
+    void* sr[2];
+    int nslices, passes, last_levels;
+};
+bool pr_tb2d_sweep_supported(const pr_ctx* ctx, int passes);
+// 3D FP32 temporally blocked kernel (fine_tb3d.cu): passes of 2..4 levels
+bool pr_tb3d_supported(const pr_ctx* ctx, int depth);
+pr_status pr_launch_fine_tb3d(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
+pr_status pr_launch_fine_tb2d_sweep(pr_ctx* ctx, const pr_sweep& sw, cudaStream_t st);
 pr_status pr_launch_energy(pr_ctx* ctx, const void* u, const void* v, int nslices,
                            double* e_host, cudaStream_t st);

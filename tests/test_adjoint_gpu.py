@@ -136,3 +136,105 @@ def test_adjoint_full_size_dot_product_3d(lib):
     rhs = float(torch.sum(u0.double() * gu0.double()) + torch.sum(p0.double() * gp0.double()))
     assert math.isfinite(lhs) and lhs > 0
     assert abs(lhs - rhs) <= 1e-4 * lhs, (lhs, rhs)
+
+
+# ---- the adjoint of the parareal solve with the correctors frozen ----------
+from oracle import parareal  # noqa: E402
+
+_CORR = {"procrustes": 0, "omega1": 1, "plain": 2}
+
+
+def _pr_case(dim, n, N, m_f, dtype, ratio, seed=3):
+    w = W.custom_case(dim, n, N, m_f, dtype, "smooth", seed=seed)
+    w.ratio = ratio
+    w.u0 = w.cast(W.periodic_gaussian(dim, n, [0.4] * dim, 0.15))
+    w.p0 = w.cast(0.3 * W.periodic_gaussian(dim, n, [0.6] * dim, 0.2))
+    return w
+
+
+def _gpu_iterate_adjoint(w, corrector, K, gu, gv, tol):
+    import torch
+    from paper_1905_00473_gb300 import binding
+    dt = torch.float32 if w.dtype == "f32" else torch.float64
+    T = lambda a: torch.tensor(a, dtype=dt, device="cuda").contiguous()
+    ctx = binding.pr_create(w.dim, w.n_fine, w.ratio, T(w.c), w.dt_f, w.dt_c, w.n_slices, w.t_final,
+                            dtype=binding.PR_F32 if w.dtype == "f32" else binding.PR_F64, tol=tol)
+    gc, gu0, gp0 = (torch.zeros(w.shape, dtype=dt, device="cuda") for _ in range(3))
+    binding.pr_iterate_adjoint(ctx, T(w.u0), T(w.p0), K, _CORR[corrector], T(gu), T(gv), gc, gu0, gp0)
+    torch.cuda.synchronize()
+    return ctx, [x.double().cpu().numpy() for x in (gu0, gp0, gc)]
+
+
+def _oracle_iterate_adjoint(w, corrector, K, gu, gv, tol):
+    P = parareal.Problem(c_fine=w.c, ratio=w.ratio, n_slices=w.n_slices, dt_com=w.dt_com, m_f=w.m_f,
+                         m_c=w.m_c, grad_order=4, tol=tol, corrector=corrector)
+    om = [(r.X, r.Y) for r in parareal.iterate(P, w.u0, w.p0, K)]
+    return adjoint.parareal_adjoint(P, w.u0, w.p0, K, om, gu, gv)
+
+
+@pytest.mark.parametrize("corrector", ["procrustes", "omega1", "plain"])
+@pytest.mark.parametrize("dim,n,N,m_f,ratio", [(1, 32, 4, 8, 2), (2, 16, 4, 8, 2), (1, 24, 3, 8, 1)])
+def test_iterate_adjoint_matches_oracle_fp64(lib, corrector, dim, n, N, m_f, ratio):
+    """K = 2 < N iterations: dL/du0, dL/dp0, dL/dc of the GPU reverse sweep
+    against the FP64 oracle adjoint (itself pinned by dot products and
+    central differences), each corrector."""
+    w = _pr_case(dim, n, N, m_f, "f64", ratio)
+    rng = np.random.default_rng(dim * 7 + n)
+    gu, gv = rng.standard_normal(w.shape), rng.standard_normal(w.shape)
+    _, got = _gpu_iterate_adjoint(w, corrector, 2, gu, gv, 1e-12)
+    ref = _oracle_iterate_adjoint(w, corrector, 2, gu, gv, 1e-12)
+    for name, g, r in zip(("u0", "p0", "c"), got, ref):
+        err = np.linalg.norm(g - r) / np.linalg.norm(r)
+        assert err <= 1e-8, (corrector, name, err)
+
+
+def test_iterate_adjoint_at_k_equal_n_is_the_serial_adjoint(lib):
+    """At K = N (finite termination) the frozen-corrector gradient equals the
+    serial fine solve's, which pr_adjoint computes."""
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = _pr_case(2, 32, 3, 8, "f64", 2)
+    rng = np.random.default_rng(5)
+    gu, gv = rng.standard_normal(w.shape), rng.standard_normal(w.shape)
+    ctx, got = _gpu_iterate_adjoint(w, "procrustes", w.n_slices, gu, gv, 1e-12)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    gc, gu0, gp0 = (torch.zeros(w.shape, dtype=torch.float64, device="cuda") for _ in range(3))
+    binding.pr_adjoint(ctx, T(w.u0), T(w.p0), T(gu), T(gv), gc, gu0, gp0)
+    for g, r in zip(got, (gu0, gp0, gc)):
+        r = r.cpu().numpy()
+        assert np.linalg.norm(g - r) <= 1e-9 * np.linalg.norm(r)
+
+
+def test_iterate_adjoint_fp32_context(lib):
+    """FP32 context (FP32 propagators and their transposes, tensor-core
+    UpdateSVD) against the FP64 oracle on the same FP32-rounded inputs."""
+    w = _pr_case(2, 64, 4, 12, "f32", 4)
+    rng = np.random.default_rng(11)
+    gu, gv = w.cast(rng.standard_normal(w.shape)), w.cast(rng.standard_normal(w.shape))
+    _, got = _gpu_iterate_adjoint(w, "procrustes", 2, gu, gv, 1e-6)
+    ref = _oracle_iterate_adjoint(w, "procrustes", 2, gu, gv, 1e-6)
+    for name, g, r in zip(("u0", "p0", "c"), got, ref):
+        err = np.linalg.norm(g - r) / np.linalg.norm(r)
+        assert err <= 2e-3, (name, err)
+
+
+def test_iterate_adjoint_3d_32_copy_of_the_differentiation_workload(lib):
+    """32^3 copy of the 3D differentiation workload (coarse 8^3, 4 slices,
+    Procrustes, K = 2 < N): plane-misfit gradient dL/dc and dL/du0 of the GPU
+    reverse sweep against the FP64 oracle adjoint, in FP64."""
+    n, N = 32, 4
+    w = W.config5(n=n)
+    w.n_slices, w.t_final = N, w.dt_com * N
+    x, y, z = W.node_coords(3, n)
+    w.p0 = np.zeros(w.shape)
+    rng = np.random.default_rng(2)
+    # dL/du(T) of 1/2 sum_{z = 0.5 plane} (u - u_target)^2 dx^2 with a seeded target
+    gu = np.zeros(w.shape)
+    gu[n // 2] = rng.standard_normal((n, n)) * (1.0 / n) ** 2
+    gv = np.zeros(w.shape)
+    w.dtype = "f64"
+    _, got = _gpu_iterate_adjoint(w, "procrustes", 2, gu, gv, 1e-12)
+    ref = _oracle_iterate_adjoint(w, "procrustes", 2, gu, gv, 1e-12)
+    for name, g, r in zip(("u0", "p0", "c"), got, ref):
+        err = np.linalg.norm(g - r) / np.linalg.norm(r)
+        assert err <= 1e-8, (name, err)

@@ -160,12 +160,19 @@ def test_first_pass_and_nine_level_last_pass(lib, n, m_f):
     w = W.custom_case(2, n, 3, m_f, "f32", "inclusion", seed=n + m_f)
     ctx = P.make_ctx(w)
     u, v = W.slice_states(w, seed=8)
-    binding.pr_profile(ctx, True)
-    _check_all(w, ctx, u, v)
-    binding.pr_profile(ctx, False)
-    fused, _ = binding.pr_profile_read(ctx, 0)
-    single, _ = binding.pr_profile_read(ctx, 1)
-    assert (fused, single) == ((m_f + 1) // 8, 0), (fused, single)
+    for one_launch in (False, True):
+        binding.pr_set_one_launch(ctx, one_launch)
+        binding.pr_profile(ctx, True)
+        _check_all(w, ctx, u, v)
+        binding.pr_profile(ctx, False)
+        fused, _ = binding.pr_profile_read(ctx, 0)
+        single, _ = binding.pr_profile_read(ctx, 1)
+        sweeps, _ = binding.pr_profile_read(ctx, 2)
+        passes = (m_f + 1) // 8
+        if one_launch and passes >= 2:   # every pass inside one launch
+            assert (fused, single, sweeps) == (0, 0, 1), (fused, single, sweeps)
+        else:
+            assert (fused, single, sweeps) == (passes, 0, 0), (fused, single, sweeps)
 
 
 @pytest.mark.parametrize("dim,n,m_f,N", [(2, 18, 9, 3), (1, 30, 11, 2), (3, 10, 5, 2)])
@@ -302,3 +309,68 @@ def test_full_size_configs(lib, cfg):
         h0 = P.modified_energy(u[s], v[s], w.c, w.dt_f, w.dx_f)
         h1 = P.modified_energy(ug[s], vg[s], w.c, w.dt_f, w.dx_f)
         assert math.isfinite(h1) and abs(h1 - h0) <= 2e-5 * abs(h0), (cfg, s, h0, h1)
+
+
+@pytest.mark.parametrize("n,N,m_f", [(1024, 5, 384), (256, 7, 20), (512, 3, 44), (128, 9, 16)])
+def test_one_launch_sweep_equals_per_pass_launches(lib, n, N, m_f):
+    """The whole sweep in one persistent launch (grid barrier between passes)
+    computes the same level recurrence in the same order as one launch per
+    pass: bit-identical outputs.  Level counts 8k + 1 (the last pass takes 9
+    levels) and 8k + 5 (a short last pass) are both covered, and the result
+    is checked against the oracle."""
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = W.custom_case(2, n, N, m_f, "f32", "inclusion")
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=4)
+    binding.pr_set_one_launch(ctx, True)
+    binding.pr_profile(ctx, True)
+    ug1, vg1 = P.run_gpu(ctx, u, v, "f32")
+    binding.pr_profile(ctx, False)
+    assert binding.pr_profile_read(ctx, 2)[0] == 1 and binding.pr_profile_read(ctx, 0)[0] == 0
+    binding.pr_set_one_launch(ctx, False)
+    ug2, vg2 = P.run_gpu(ctx, u, v, "f32")
+    assert np.array_equal(ug1, ug2) and np.array_equal(vg1, vg2)
+    for s in (0, N - 1):
+        ur, vr = P.oracle_slice(w, u[s], v[s])
+        assert P.slice_errors(w, ug1[s], vg1[s], ur, vr)[0] <= P.TOL_ENERGY_F32
+
+
+@pytest.mark.parametrize("n,N,m_f", [(64, 3, 7), (64, 2, 10), (128, 2, 12), (64, 4, 3)])
+def test_fused_3d_passes_match_oracle(lib, n, N, m_f):
+    """3D FP32 at depth 4 (2.5D blocking: xy tiles of 64 x 16 with a 4-point
+    halo, z streamed): 8, 11, 13 and 4 levels give full passes, a short last
+    pass and the final one-level pass, with the periodic wrap in x, y and z
+    crossing tile boundaries; every slice against the oracle."""
+    from paper_1905_00473_gb300 import binding
+    w = W.custom_case(3, n, N, m_f, "f32", "smooth", seed=30 + n + m_f)
+    ctx = P.make_ctx(w)
+    assert binding.pr_info(ctx)["block_depth"] == 4
+    u, v = W.slice_states(w, seed=5)
+    binding.pr_profile(ctx, True)
+    _check_all(w, ctx, u, v)
+    binding.pr_profile(ctx, False)
+    levels = m_f + 1
+    assert binding.pr_profile_read(ctx, 0)[0] == levels // 4 + (1 if levels % 4 > 1 else 0)
+    assert binding.pr_profile_read(ctx, 1)[0] == (1 if levels % 4 == 1 else 0)
+
+
+def test_fused_3d_inclusion_medium(lib):
+    """The discontinuous medium in 3D (c = 3 inside [0.3, 0.7]^3) at depth 4."""
+    w = W.custom_case(3, 64, 2, 9, "f32", "inclusion", seed=3)
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=9)
+    _check_all(w, ctx, u, v)
+
+
+def test_fused_3d_full_size_sampled(lib):
+    """The 3D differentiation workload's sweep at full size (256^3, 32 slices,
+    m_F = 64, depth 4): two sampled slices against the oracle."""
+    w = W.config5()
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=0)
+    ug, vg = P.run_gpu(ctx, u, v, w.dtype)
+    for s in (3, 30):
+        ur, vr = P.oracle_slice(w, u[s], v[s])
+        e, l2 = P.slice_errors(w, ug[s], vg[s], ur, vr)
+        assert e <= P.TOL_ENERGY_F32 and l2 <= P.TOL_ENERGY_F32, (s, e, l2)
