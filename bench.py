@@ -366,8 +366,9 @@ def parareal_time_to_tol(dev, tol_err: float = 1e-4, k_max: int = 32, svd_tol: f
     e_ref = binding.pr_energy(ctx1, ref[N].contiguous(), refv[N].contiguous())[0]
     us = torch.zeros_like(ref)
     vs = torch.zeros_like(ref)
-    # warm-up: library initialisation (cuFFT plans, cuBLAS/cuSOLVER handles)
-    binding.pr_iterate(ctx, u0, p0, 1, binding.PR_CORR_PROCRUSTES, us, vs)
+    # warm-up: library initialisation (cuFFT plans, cuBLAS/cuSOLVER handles and
+    # the solvers' first calls at every size the run reaches)
+    binding.pr_iterate(ctx, u0, p0, k_max, binding.PR_CORR_PROCRUSTES, us, vs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     out = binding.pr_iterate(ctx, u0, p0, k_max, binding.PR_CORR_PROCRUSTES, us, vs,
@@ -395,12 +396,18 @@ def run_batch(a) -> int:
     graph launch.  Slice states: the instance's Gaussian u0 rolled by a seeded
     shift per slice, u_t = 0 (cheap to build for the large instances)."""
     import numpy as np
+    rank, world, local = dist_env()
+    ws = [W.config4_instance(i) for i in range(a.instances)]
+    # the oracle pool is spawned before any CUDA call; it samples the
+    # smallest instance (its cost per point-update is that of every instance)
+    smp = None
+    if not a.no_cpu_baseline:
+        wsmall = min(ws, key=lambda x: x.points)
+        smp = OracleSampler(wsmall, oracle_procs(), oracle_steps(wsmall))
     import torch
     from paper_1905_00473_gb300 import binding
-    rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    ws = [W.config4_instance(i) for i in range(a.instances)]
     ctxs, ui, vi, uo, vo = [], [], [], [], []
     units = 0
     for w in ws:
@@ -421,13 +428,33 @@ def run_batch(a) -> int:
     for _ in range(a.warmup):
         batch.launch()
     torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(a.steps):
         batch.launch()
     e1.record()
     torch.cuda.synchronize()
+    clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    # roofline of the whole graph: every instance's algorithmic traffic (20 B
+    # per point per HBM pass) over the graph's time per step
+    depths = [batch.info(i)[0] for i in range(len(ws))]
+    passes = [hbm_passes(w.m_f, d) for w, d in zip(ws, depths)]
+    step_bytes = sum(ALGO_BYTES_PER_POINT_PASS * w.points * w.n_slices * pz for w, pz in zip(ws, passes))
+    peak, peak_src = measured_peak()
+    achieved = step_bytes / (ms / a.steps * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "the batch graph (every instance's passes)", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+            "algorithmic_bytes_per_launch": step_bytes, "mean_launch_ms": ms / a.steps}
+    cpu = None
+    if smp is not None:
+        try:
+            cpu = smp.baseline()
+        finally:
+            smp.close()
     line = {"metric": "fine grid-point updates/s", "value": units * a.steps / (ms * 1e-3),
             "unit": "point-updates/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -437,7 +464,9 @@ def run_batch(a) -> int:
                                       "depth": batch.info(i)[0], "columns": batch.info(i)[1]}
                                      for i, w in enumerate(ws)],
                        "point_updates_per_step": units, "autotune_s": tune_s,
-                       "graph": "one CUDA graph, 8 streams"}}
+                       "graph": "one CUDA graph, 8 streams"},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": a.steps * sum(passes)}   # one launch per pass in the batch graph
     print(json.dumps(line), flush=True)
     return 0
 
@@ -655,8 +684,9 @@ def main(argv=None) -> int:
     ap.add_argument("--instances", type=int, default=8, help="--config 4: instances in the batch")
     ap.add_argument("--no-parareal", action="store_true",
                     help="skip the parareal time-to-1e-4 measurement")
-    ap.add_argument("--one-launch", choices=["on", "off"], default="on",
-                    help="on: a whole sweep in one persistent launch where supported; off: one launch per pass")
+    ap.add_argument("--one-launch", choices=["on", "off"], default="off",
+                    help="on: a whole sweep in one persistent launch where supported; off (library default): "
+                         "one launch per pass")
     ap.add_argument("--l2-flush", choices=["auto", "on", "off"], default="auto",
                     help="auto: flush L2 between timed steps when the inputs are smaller than 2x L2")
     a = ap.parse_args(argv)

@@ -297,7 +297,8 @@ typedef struct pr_batch pr_batch;
  *             instance's context); 0: keep each context's settings.
  * Then captures all sweeps into one CUDA graph: one branch per instance,
  * biggest first, spread over 8 library-owned streams between a fork and a
- * join.  Runs (and synchronises) the timing sweeps; the bound arrays must
+ * join (one launch per pass: pr_set_one_launch is switched off for the
+ * bound contexts, whose sweeps run concurrently).  Runs (and synchronises) the timing sweeps; the bound arrays must
  * stay valid until pr_batch_destroy.  The contexts must not be used
  * concurrently with a launch of the batch.  PR_EINVAL if a context appears
  * twice or an output array overlaps an array of another instance (inputs may
@@ -327,13 +328,15 @@ void pr_batch_destroy(pr_batch* b);
  * Takes effect at the next call. */
 pr_status pr_set_fused_columns(pr_ctx* ctx, int columns);
 
-/* pr_set_one_launch -- on != 0 (the default): where the fused 2D kernel runs
- * whole rows at depth 8 with four columns per thread (n = 128 .. 1024) and a
- * sweep takes at least two passes, pr_fine_all_slices runs every pass of the
- * sweep (all slices) in ONE persistent cooperative launch, one CTA per SM, with
- * a bounded grid-wide barrier between passes; on == 0: one launch per pass.
- * Both compute the same level recurrence in the same order (bit-identical
- * results).  Takes effect at the next call. */
+/* pr_set_one_launch -- on != 0: where the fused 2D kernel runs whole rows at
+ * depth 8 with four columns per thread (n = 128 .. 1024) and a sweep takes at
+ * least two passes, pr_fine_all_slices runs every pass of the sweep (all
+ * slices) in ONE persistent cooperative launch, one CTA per SM, with a
+ * bounded grid-wide barrier between passes; on == 0 (the default): one launch
+ * per pass, which measured faster on a GB300 (the pass loop costs the
+ * middle-pass body its kappa register ring).  Both compute the same level
+ * recurrence in the same order (bit-identical results).  Takes effect at the
+ * next call. */
 pr_status pr_set_one_launch(pr_ctx* ctx, int on);
 
 /* pr_debug_stall_waits -- test hook for the time-out path.  While enabled,

@@ -119,6 +119,10 @@ extern "C" pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void*
                 }
             }
     }
+    // the instances' sweeps run concurrently on several streams: each takes one
+    // launch per pass (a whole-sweep cooperative launch holds every SM and
+    // waits at grid barriers, which concurrent launches must not share)
+    for (int i = 0; i < count; ++i) b->ctx[i]->one_launch = 0;
     // autotuner: the fastest instantiated (depth, columns) per instance, timed once
     if (autotune) {
         const int cands[5][2] = {{8, 4}, {8, 2}, {4, 4}, {4, 2}, {1, 0}};

@@ -23,13 +23,14 @@
 // (overlapped tiling: the halo is recomputed by the neighbouring tiles).
 //
 // Loads.  Every thread stages its own quads of plane i + 2 (u_hi, u_t,
-// residual) into a three-plane shared ring with cp.async (no other thread
-// reads them, so its own wait_group orders them); kappa is read per level
-// through the read-only path (the planes a CTA touches stay in L1/L2).
+// residual, kappa) into shared rings with cp.async (no other thread reads
+// them, so its own wait_group orders them): three planes of u_hi, u_t and
+// residual, twelve of kappa, which the levels read up to four steps later.
 //
 // Rings.  The plane loop is unrolled 12-fold; every ring period divides it:
 // the du rings of the levels and the u_hi ring (3), the u_t and shared-tile
-// parities (2), the D0 ring (4) and the staging ring (3).
+// parities (2), the D0 ring (4) and the staging rings (3, 12).  Plane
+// indices advance by one per step, so their periodic wrap is a compare.
 #include "pr_internal.cuh"
 
 namespace {
@@ -60,6 +61,7 @@ struct __align__(16) Smem3 {
     float su[3][EY][EX];         // staged u_hi, u_t (by plane mod 3)
     float sv[3][EY][EX];
     uint16_t sr[3][EY][EX];      // staged residual
+    float sk[12][EY][EX];        // staged kappa (by plane mod 12: read by the levels up to 4 steps later)
 };
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -76,10 +78,19 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 
 struct Item {
     int64_t base;    // slice offset + row offset of this thread's quad (without z)
+    int64_t kbase;   // the same offset in kappa (no slice)
     int64_t n2;      // n * n
     int gx0, gy;     // global x of the quad's first point, global y of the row
     bool inner;      // the quad lies in the interior tile
 };
+
+// z - k wrapped into [0, n) for 0 <= z < n, -n < -k <= n
+__device__ __forceinline__ int zwrap(int z, int k, int n) {
+    int r = z + k;
+    if (r >= n) r -= n;
+    if (r < 0) r += n;
+    return r;
+}
 
 // global plane z of local plane p of a column with L levels of halo
 __device__ __forceinline__ int plane_z(int p, int L, int n) {
@@ -88,9 +99,10 @@ __device__ __forceinline__ int plane_z(int p, int L, int n) {
 }
 
 // One step of the plane pipeline at ring position i (K = i mod 12).
+// zi: global z of plane i (the arriving plane; planes wrap periodically)
 template <int K>
-__device__ __forceinline__ void tb3d_step(const Tb3dParams& p, Smem3& sm, const Item& it, int i, int nload, int L,
-                                          float (&R)[B3][3][4], float (&VV)[B3][2][4], float (&UH)[3][4],
+__device__ __forceinline__ void tb3d_step(const Tb3dParams& p, Smem3& sm, const Item& it, int i, int zi, int nload,
+                                          int L, float (&R)[B3][3][4], float (&VV)[B3][2][4], float (&UH)[3][4],
                                           float (&DR)[4][4]) {
     constexpr int CUR = K % 3, PRV = (K + 2) % 3, NXT = (K + 1) % 3;
     constexpr int PAR = K & 1, PPAR = PAR ^ 1;
@@ -101,11 +113,13 @@ __device__ __forceinline__ void tb3d_step(const Tb3dParams& p, Smem3& sm, const 
     {
         const int q = i + kPF;
         if (q < nload) {
-            constexpr int SS = (K + kPF) % 3;
-            const int64_t off = it.base + (int64_t)plane_z(q, L, n) * it.n2;
+            constexpr int SS = (K + kPF) % 3, SK = (K + kPF) % 12;
+            const int64_t zq = zwrap(zi, kPF, n);
+            const int64_t off = it.base + zq * it.n2;
             cp_async16(&sm.su[SS][ey][lx], p.u_in + off);
             cp_async16(&sm.sv[SS][ey][lx], p.v_in + off);
             if (p.r_in) cp_async8(&sm.sr[SS][ey][lx], p.r_in + off);
+            cp_async16(&sm.sk[SK][ey][lx], p.kap + it.kbase + zq * it.n2);
         }
         cp_commit();
         cp_wait<kPF>();
@@ -117,7 +131,7 @@ __device__ __forceinline__ void tb3d_step(const Tb3dParams& p, Smem3& sm, const 
     int64_t off_out = 0;
     float4 u0o = make_float4(0.f, 0.f, 0.f, 0.f);
     if (do_out) {
-        off_out = it.base + (int64_t)plane_z(p_out, L, n) * it.n2;
+        off_out = it.base + (int64_t)zwrap(zi, -B3, n) * it.n2;
         u0o = __ldcs((const float4*)(p.u_in + off_out));
     }
 
@@ -175,13 +189,11 @@ __device__ __forceinline__ void tb3d_step(const Tb3dParams& p, Smem3& sm, const 
     float dout[4], vout[4];
 #pragma unroll
     for (int l = 0; l < B3; ++l) {
-        const int r = i - 1 - l;
         const float* C = R[l][CUR];
         float vn[4], dn[4];
         if (l < L) {
-            // kappa of plane r at the thread's points (kappa has no slice offset)
-            const int64_t koff = (int64_t)plane_z(r, L, n) * it.n2 + (int64_t)it.gy * n + it.gx0;
-            const float4 kq = __ldg((const float4*)(p.kap + koff));
+            // kappa of plane r = i-1-l at the thread's points, staged with the plane
+            const float4 kq = *(const float4*)&sm.sk[(K + 11 - l) % 12][ey][lx];
             float kk[4] = {kq.x, kq.y, kq.z, kq.w};
             const int g = p.g0 + l;
             const float wk = (g == 0 || g == p.m) ? 0.5f : 1.0f;
@@ -266,7 +278,8 @@ __global__ void __launch_bounds__(NT3, 1) fine_tb3d_kernel(const Tb3dParams p) {
         it.gx0 = (tx * TX - B3 + 4 * qx + n) % n;
         it.gy = (ty * TY - B3 + ey + n) % n;
         it.inner = qx >= B3 / 4 && qx < B3 / 4 + TX / 4 && ey >= B3 && ey < B3 + TY;
-        it.base = slice * it.n2 * n + (int64_t)it.gy * n + it.gx0;
+        it.kbase = (int64_t)it.gy * n + it.gx0;
+        it.base = slice * it.n2 * n + it.kbase;
         float R[B3][3][4], VV[B3][2][4], UH[3][4], DR[4][4];
 #pragma unroll
         for (int l = 0; l < B3; ++l)
@@ -284,18 +297,21 @@ __global__ void __launch_bounds__(NT3, 1) fine_tb3d_kernel(const Tb3dParams p) {
 #pragma unroll
         for (int q = 0; q < kPF; ++q) {
             if (q < nload) {
-                const int64_t off = it.base + (int64_t)plane_z(q, L, n) * it.n2;
+                const int64_t zq = plane_z(q, L, n);
+                const int64_t off = it.base + zq * it.n2;
                 cp_async16(&sm.su[q % 3][ey][4 * qx], p.u_in + off);
                 cp_async16(&sm.sv[q % 3][ey][4 * qx], p.v_in + off);
                 if (p.r_in) cp_async8(&sm.sr[q % 3][ey][4 * qx], p.r_in + off);
+                cp_async16(&sm.sk[q % 12][ey][4 * qx], p.kap + it.kbase + zq * it.n2);
             }
             cp_commit();
         }
-        int i = 0;
+        int i = 0, zi = plane_z(0, L, n);
 #define PR_TB3D_STEP(K)                                                     \
     if (i >= niter) break;                                                   \
-    tb3d_step<K>(p, sm, it, i, nload, L, R, VV, UH, DR);                     \
-    ++i;
+    tb3d_step<K>(p, sm, it, i, zi, nload, L, R, VV, UH, DR);                 \
+    ++i;                                                                     \
+    zi = zi + 1 == n ? 0 : zi + 1;
         for (;;) {
             PR_TB3D_STEP(0) PR_TB3D_STEP(1) PR_TB3D_STEP(2) PR_TB3D_STEP(3) PR_TB3D_STEP(4) PR_TB3D_STEP(5)
             PR_TB3D_STEP(6) PR_TB3D_STEP(7) PR_TB3D_STEP(8) PR_TB3D_STEP(9) PR_TB3D_STEP(10) PR_TB3D_STEP(11)

@@ -44,7 +44,7 @@ struct pr_ctx {
     int64_t partials_len = 0;
     int* dev_flag = nullptr;        // device-side error flag (bounded waits)
     unsigned int* sweep_ctr = nullptr;   // grid-barrier counter of the one-launch sweep
-    int one_launch = 1;             // run a supported sweep as one persistent launch
+    int one_launch = 0;             // run a supported sweep as one persistent launch (pr_set_one_launch)
     std::string err;
     // pr_profile: event pairs around launches, by kernel kind
     bool prof_on = false;

@@ -270,9 +270,17 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
     float4 u0o = make_float4(0.f, 0.f, 0.f, 0.f);
     if (do_out) {
         off_out = sg.slice_off + (int64_t)seg_row(sg.ylo, rho_out, n) * n + sg.x0 + kCpt * t;
-        // in a whole-sweep launch the input was written by other CTAs in the
-        // previous pass: read it from L2, past this SM's L1
-        u0o = SWEEP ? __ldcg((const float4*)(p.u_in + off_out)) : __ldcs((const float4*)(p.u_in + off_out));
+        if constexpr (SWEEP) {
+            // in a whole-sweep launch the input was written by other CTAs in
+            // the previous pass: read it from L2, past this SM's L1, marked
+            // evict-first there like the streamed rows
+            const uint64_t ef = policy(0);
+            asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                         : "=f"(u0o.x), "=f"(u0o.y), "=f"(u0o.z), "=f"(u0o.w)
+                         : "l"(p.u_in + off_out), "l"(ef));
+        } else {
+            u0o = __ldcs((const float4*)(p.u_in + off_out));
+        }
     }
 
     // ---- load stage: row i arrives; D0 of row i-1 -------------------------

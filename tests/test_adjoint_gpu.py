@@ -238,3 +238,25 @@ def test_iterate_adjoint_3d_32_copy_of_the_differentiation_workload(lib):
     for name, g, r in zip(("u0", "p0", "c"), got, ref):
         err = np.linalg.norm(g - r) / np.linalg.norm(r)
         assert err <= 1e-8, (name, err)
+
+
+@pytest.mark.parametrize("corrector,K", [("plain", 2), ("omega1", 2), ("procrustes", 3)])
+def test_parareal_autograd_gradcheck(lib, corrector, K):
+    """torch.autograd.gradcheck of PararealSolve in FP64 on a tiny 2D case:
+    with the plain and Omega = 1 correctors the forward map has no data-driven
+    corrector, and with Procrustes K = N makes the result independent of the
+    corrector, so central differences of the forward see the same map as the
+    frozen-corrector adjoint."""
+    import torch
+    from paper_1905_00473_gb300 import autograd, binding
+    w = _pr_case(2, 8, 3, 4, "f64", 2)
+    rng = np.random.default_rng(4)
+    c = torch.tensor(w.c, device="cuda", requires_grad=True)
+    u0 = torch.tensor(rng.standard_normal(w.shape), device="cuda", requires_grad=True)
+    p0 = torch.tensor(rng.standard_normal(w.shape), device="cuda", requires_grad=True)
+
+    def f(c_, a, b):
+        return autograd.parareal_solve(c_, a, b, w.ratio, w.dt_f, w.dt_c, w.n_slices, w.t_final, K,
+                                       _CORR[corrector], 1e-12, 4)
+
+    assert torch.autograd.gradcheck(f, (c, u0, p0), eps=1e-6, atol=1e-7, rtol=1e-5)

@@ -21,6 +21,7 @@ def test_bounded_wait_times_out_and_context_recovers(lib, n, m_f):
     w = W.custom_case(2, n, 2, m_f, "f32", "smooth")
     ctx = P.make_ctx(w)
     assert binding.pr_info(ctx)["block_depth"] == 8
+    binding.pr_set_one_launch(ctx, m_f == 23)
     u, v = W.slice_states(w, seed=1)
     ud = torch.tensor(u, dtype=torch.float32, device="cuda")
     vd = torch.tensor(v, dtype=torch.float32, device="cuda")
