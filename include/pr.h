@@ -157,7 +157,7 @@ pr_status pr_coarse_sweep(pr_ctx* ctx, const void* u, const void* v, void* U_out
  * Fine sweeps run in the context dtype; Lambda, Omega, Lambda^dagger, I, the
  * data matrices and the SVD in FP64 (cuFFT, cuBLAS, cuSOLVER for the FFTs and
  * the dense factorisations).  In FP32 contexts the tall products of UpdateSVD
- * with the kept bases run on the tensor cores in 3xTF32 (see
+ * with the kept bases run on the tensor cores in split-TF32 (see
  * pr_snapshot_project) with one reorthogonalisation pass, and the SVD of the
  * small matrix H is taken from the symmetric eigenproblem of H^T H when every
  * kept singular value is at least 1e-6 of the largest (else FP64 gesvd).  The correction of a slice is applied to the
@@ -233,9 +233,10 @@ pr_status pr_adjoint(pr_ctx* ctx, const void* u0, const void* p0, const void* gu
  * data onto the kept bases, U_F = U^T F, V_G = V^T G, and the deflations
  * F - U U_F, G - V V_G.  They run on the tcgen05 tensor cores: operands are
  * FP64 in device memory, split while staged into shared memory into two
- * TF32 halves (x = hi + lo), and each product is formed as hi*hi + hi*lo +
- * lo*hi with FP32 accumulation ("3xTF32": about 2^-21 relative error per
- * product, FP32-level accuracy).  pr_iterate uses them in FP32 contexts
+ * TF32 values carrying the leading 11 + 11 significant bits (x = hi + lo),
+ * and each product is formed as hi*hi + hi*lo + lo*hi + lo*lo with FP32
+ * accumulation ("split-TF32": about 2^-21 relative error per product,
+ * FP32-level accuracy).  pr_iterate uses them in FP32 contexts
  * (FP64 contexts keep FP64 DGEMM).  The context supplies the device error
  * flag of the bounded waits (reported by pr_check) and error messages; its
  * grid is not used.  Arrays are DEVICE double, column-major, 8-byte aligned;

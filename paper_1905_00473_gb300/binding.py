@@ -400,7 +400,7 @@ def _f64_matrix(name: str, t, rows: int, cols: int):
 
 
 def pr_snapshot_project(ctx: Context, A, B, C, stream=None) -> None:
-    """C = A^T B on the tensor cores (3xTF32).  Column-major matrices are
+    """C = A^T B on the tensor cores (split-TF32).  Column-major matrices are
     passed as tensors of shape (columns, rows): A (M, K), B (N, K), C (N, M)."""
     M, K = int(A.shape[0]), int(A.shape[1])
     N = int(B.shape[0])
@@ -412,7 +412,7 @@ def pr_snapshot_project(ctx: Context, A, B, C, stream=None) -> None:
 
 
 def pr_snapshot_deflate(ctx: Context, A, T, F, O, stream=None) -> None:
-    """O = F - A T on the tensor cores (3xTF32).  Shapes (columns, rows):
+    """O = F - A T on the tensor cores (split-TF32).  Shapes (columns, rows):
     A (K, M), T (N, K), F and O (N, M)."""
     K, M = int(A.shape[0]), int(A.shape[1])
     N = int(F.shape[0])

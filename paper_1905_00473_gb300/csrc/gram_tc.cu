@@ -10,17 +10,18 @@
 // update; N (the number of new columns, at most 64 per launch) is small.
 //
 // Precision.  Operands stay FP64 in HBM.  Each element x is split while it
-// is staged into shared memory as x = hi + lo, hi = tf32(x) (round to
-// nearest), lo = tf32(x - hi), and every product is formed as
-// hi*hi + hi*lo + lo*hi by three kind::tf32 MMAs into one FP32 accumulator
-// ("3xTF32"): about 2^-21 relative per product, FP32-level, against TF32's
-// 2^-11.  Partial sums leave tensor memory in FP32 and are combined in FP64.
+// is staged into shared memory as x = hi + lo (two tf32 values carrying the
+// leading 11 + 11 significant bits, |x - hi - lo| <= 2^-21 |x|), and every
+// product is formed as hi*hi + hi*lo + lo*hi + lo*lo by kind::tf32 MMAs into
+// one FP32 accumulator: about 2^-21 relative per product, FP32-level, against
+// TF32's 2^-11.  Partial sums leave tensor memory in FP32 and are combined in
+// FP64.
 //
 // Kernel shape.  128 threads per CTA; thread t owns tile row t (the M = 128
 // accumulator rows map onto the 128 tensor-memory lanes, warp w reads lanes
 // 32w..32w+31).  K advances in chunks of 32 elements: the threads load the
 // chunk's FP64 values, split them and store hi and lo into 128-byte-swizzled
-// K-major tiles (two stages), then thread 0 issues 4 K-steps x 3 MMAs and
+// K-major tiles (two stages), then thread 0 issues 4 K-steps x 4 MMAs and
 // commits them to the stage's mbarrier, which the threads wait on before
 // they overwrite that stage.  The loads of the next chunk are issued before
 // that wait, so HBM traffic overlaps the MMAs.  Every wait is bounded.
@@ -71,12 +72,30 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, uint64_t 
     return true;
 }
 
-// tf32 split of one FP64 value: hi = tf32(x) rounded to nearest, lo = tf32(x - hi)
+// tf32 split of one FP64 value by integer operations on its bits (no FP64
+// arithmetic, which runs at a small fraction of the FP32 rate on this GPU):
+// hi = x with its mantissa truncated to tf32's 10 bits, lo = the next 10
+// significant bits of the remainder x - hi (same sign), so that
+// |x - hi - lo| <= 2^-21 |x|.  Values below the float range (|x| < 2^-126)
+// become 0; the operands here are O(1e-3..1e3).
 __device__ __forceinline__ void split_tf32(double x, uint32_t& hi, uint32_t& lo) {
-    const float xf = (float)x;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(xf));
-    const float r = (float)(x - (double)__uint_as_float(hi));
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t s = (uint32_t)(b >> 63) << 31;
+    const int E = (int)((b >> 52) & 0x7ff);
+    const uint64_t M = b & 0xFFFFFFFFFFFFFull;
+    const int Ef = E - 1023 + 127;
+    if (E == 0 || Ef <= 0) {
+        hi = lo = 0u;
+        return;
+    }
+    hi = s | ((uint32_t)Ef << 23) | ((uint32_t)(M >> 42) << 13);
+    const uint64_t R = M & ((1ull << 42) - 1);   // remainder R * 2^(E - 1075)
+    lo = 0u;
+    if (R != 0) {
+        const int lz = __clzll((long long)R);    // 22 .. 63
+        const int Elo = (63 - lz) + E - 1075 + 127;
+        if (Elo > 0) lo = s | ((uint32_t)Elo << 23) | ((uint32_t)((R << (lz + 1)) >> 54) << 13);
+    }
 }
 
 // Byte offset of the 16-byte group c (K elements 4c..4c+3) of row m in a
@@ -293,6 +312,7 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramArgs g) {
                 mma_tf32(tmem, sdesc(a_hi + off), sdesc(b_hi + off), idesc, acc0);
                 mma_tf32(tmem, sdesc(a_hi + off), sdesc(b_lo + off), idesc, 1u);
                 mma_tf32(tmem, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
+                mma_tf32(tmem, sdesc(a_lo + off), sdesc(b_lo + off), idesc, 1u);
             }
             mma_commit(&bars[s]);
         }
@@ -376,7 +396,7 @@ int sm_count() {
 }  // namespace
 
 // C (M x N, column-major, ldc) = A^T B with A (K x M, lda), B (K x N, ldb),
-// all FP64, on the tensor cores in 3xTF32 (see the file comment).
+// all FP64, on the tensor cores in split-TF32 (see the file comment).
 pr_status tc_gram_launch(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t K, int64_t M, int N,
                          double* C, int64_t ldc, int* flag, cudaStream_t st) {
     if (M <= 0 || N <= 0) return PR_OK;
@@ -406,7 +426,7 @@ pr_status tc_gram_launch(const double* A, int64_t lda, const double* B, int64_t 
 }
 
 // O (M x N, ldo) = F (M x N, ldf) - A T with A (M x K, lda) and T (K x N,
-// ldt), all FP64, on the tensor cores in 3xTF32.  O may equal F.
+// ldt), all FP64, on the tensor cores in split-TF32.  O may equal F.
 pr_status tc_update_launch(const double* A, int64_t lda, const double* T, int64_t ldt, const double* F, int64_t ldf,
                            int64_t M, int64_t K, int N, double* O, int64_t ldo, int* flag, cudaStream_t st) {
     if (M <= 0 || N <= 0) return PR_OK;

@@ -349,7 +349,7 @@ struct pr_driver {
     int64_t work_len = 0;
     int hcap = 0;   // allocated (s+N) capacity of the small matrices
     // FP32 contexts: the tall-skinny products with the bases (projections
-    // and deflations of Alg. 1) run on the tensor cores in 3xTF32
+    // and deflations of Alg. 1) run on the tensor cores in split-TF32
     // (gram_tc.cu), with one reorthogonalisation pass; FP64 contexts use
     // FP64 DGEMM throughout
     bool tc = false;

@@ -68,7 +68,7 @@ void pr_driver_free(pr_ctx* ctx);
 pr_status pr_slice_adjoint(pr_ctx* c, const void* u_in, const void* v_in, void* lu, void* lv, double* gk,
                            cudaStream_t st);
 
-// ---- snapshot products on the tensor cores (gram_tc.cu, 3xTF32) -------------
+// ---- snapshot products on the tensor cores (gram_tc.cu, split-TF32) -------------
 // C (M x N, ldc) = A^T B, A (K x M, lda), B (K x N, ldb); C is overwritten.
 pr_status tc_gram_launch(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t K, int64_t M, int N,
                          double* C, int64_t ldc, int* flag, cudaStream_t st);

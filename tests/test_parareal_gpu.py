@@ -284,7 +284,7 @@ def test_config2_iterations_match_oracle_fp32(lib):
 
 
 def test_update_svd_fp32_context_matches_oracle(lib):
-    """UpdateSVD of an FP32 context (tensor-core 3xTF32 projections and
+    """UpdateSVD of an FP32 context (tensor-core split-TF32 projections and
     deflations, reorthogonalised) against the FP64 oracle: three updates of
     well-conditioned data, Omega g to 1e-6 relative."""
     import torch

@@ -1,7 +1,7 @@
 """The tensor-core snapshot products of UpdateSVD (Alg. 1: U^T F and
 F - U U_F) through the C ABI, against FP64 numpy on the same inputs.
 
-The products are formed in 3xTF32 with FP32 accumulation: the bound used
+The products are formed in split-TF32 with FP32 accumulation: the bound used
 here, 1e-5 of |A_m| |B_n| per entry (Cauchy-Schwarz scale of the entry),
 sits an order above the expected 2^-21 per product plus the FP32
 accumulation error, and two orders below what one TF32 pass (2^-11) gives.
