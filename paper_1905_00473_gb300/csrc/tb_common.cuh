@@ -170,12 +170,14 @@ struct Tb2dParams {
 // phi(r) = r + K * (slice boundaries below r) the cut points are where phi
 // crosses multiples of phi_total / G (inside a boundary's jump the cut falls
 // on the boundary itself).
-__device__ __forceinline__ int64_t balanced_row(int64_t rows_total, int n, int K, int64_t b, int64_t G) {
+// (host and device: the CPU tests compile it into a host harness)
+__host__ __device__ __forceinline__ int64_t balanced_row(int64_t rows_total, int n, int K, int64_t b, int64_t G) {
     const int64_t slices = rows_total / n;
     const int64_t phi = (rows_total + (slices - 1) * K) * b / G;
     const int64_t j = phi / (n + K);
-    const int64_t r = min(phi - j * K, (j + 1) * (int64_t)n);
-    return min(r, rows_total);
+    const int64_t a = phi - j * K, c = (j + 1) * (int64_t)n;
+    const int64_t r = a < c ? a : c;
+    return r < rows_total ? r : rows_total;
 }
 
 // Global row of local row rho of a segment whose first local row is ylo

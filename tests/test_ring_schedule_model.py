@@ -26,7 +26,10 @@ not finished.
 """
 import random
 
-KU, KRS, KPRE = 12, 6, 2
+from tests._shipped import header_constant
+
+# the ring sizes and the prefetch distance of the shipped kernel
+KU, KRS, KPRE = (header_constant("tb2d_kernels.cuh", k) for k in ("kU", "kRS", "kPre"))
 
 
 def run(segments, B, even=False):
