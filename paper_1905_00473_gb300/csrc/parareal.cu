@@ -114,56 +114,83 @@ __global__ void lambda_kernel(const T* __restrict__ w, const T* __restrict__ wt,
     }
 }
 
-// zero mode of grad2func for the difference: sum_J (w_J - U_J) (one block, fixed order)
+// zero mode of grad2func for the difference: sum_J (w_J - U_J).  kZm blocks
+// each reduce a fixed share in a fixed order into zbuf[1 + b]; the block that
+// finishes last adds the partials in block order into zbuf[0] and resets the
+// arrival counter (after the partials), so the sum is the same on every run.
+constexpr int kZm = 64;
 template <typename T>
-__global__ void zero_mode_kernel(const T* __restrict__ w, const T* __restrict__ U, int64_t cpts,
-                                 double* __restrict__ out) {
-    __shared__ double red[1024];
+__global__ void __launch_bounds__(kT) zero_mode_kernel(const T* __restrict__ w, const T* __restrict__ U,
+                                                       int64_t cpts, double* __restrict__ zbuf) {
+    __shared__ double red[kT];
+    __shared__ bool last;
     double acc = 0.0;
-    for (int64_t j = threadIdx.x; j < cpts; j += blockDim.x) acc += (double)w[j] - (U ? (double)U[j] : 0.0);
+    for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < cpts; j += (int64_t)gridDim.x * kT)
+        acc += (double)w[j] - (U ? (double)U[j] : 0.0);
     red[threadIdx.x] = acc;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    for (int s = kT / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = red[0];
+    unsigned* count = (unsigned*)(zbuf + 1 + kZm);
+    if (threadIdx.x == 0) {
+        zbuf[1 + blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double sum = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) sum += __ldcg(zbuf + 1 + b);
+        zbuf[0] = sum;
+        *count = 0u;
+    }
 }
 
 // ---------------------------------------------------------------- Lambda^dagger (grad2func)
-__global__ void real_to_complex(const double* __restrict__ x, cufftDoubleComplex* __restrict__ z, int64_t m) {
+// CT: the transform's complex type, double2 (FP64 contexts, adjoints) or
+// float2 (the forward path of FP32 contexts); real_of<CT> its real type
+template <typename CT>
+using real_of = decltype(CT::x);
+
+template <typename CT>
+__global__ void real_to_complex(const double* __restrict__ x, CT* __restrict__ z, int64_t m) {
+    using RT = real_of<CT>;
     for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT)
-        z[j] = make_cuDoubleComplex(x[j], 0.0);
+        z[j] = CT{(RT)x[j], (RT)0};
 }
 
 // w^(xi) = -i (xi . q^) / |xi|^2, w^(0) = zero mode (Alg. 2), in place into z[0..cpts)
-template <int DIM>
-__global__ void grad2func_combine(cufftDoubleComplex* __restrict__ z, int64_t nc, int64_t cpts,
-                                  const double* __restrict__ zero_mode) {
+template <int DIM, typename CT>
+__global__ void grad2func_combine(CT* __restrict__ z, int64_t nc, int64_t cpts, const double* __restrict__ zero_mode) {
+    using RT = real_of<CT>;
     for (int64_t J = (int64_t)blockIdx.x * kT + threadIdx.x; J < cpts; J += (int64_t)gridDim.x * kT) {
         int64_t c[3];
         coords<DIM>(J, nc, c);
-        double re = 0.0, im = 0.0, mag2 = 0.0;
+        RT re = 0, im = 0, mag2 = 0;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            const double xi = 2.0 * M_PI * (double)freq(c[a], nc);
-            const cufftDoubleComplex q = z[a * cpts + J];
+            const RT xi = (RT)(2.0 * M_PI * (double)freq(c[a], nc));
+            const CT q = z[a * cpts + J];
             re += xi * q.x;
             im += xi * q.y;
             mag2 += xi * xi;
         }
         // -i (re + i im) = im - i re
-        z[J] = mag2 > 0 ? make_cuDoubleComplex(im / mag2, -re / mag2) : make_cuDoubleComplex(*zero_mode, 0.0);
+        z[J] = mag2 > 0 ? CT{im / mag2, -re / mag2} : CT{(RT)*zero_mode, (RT)0};
     }
 }
 
 // du = real(ifft(.)) (unnormalised inverse, so / cpts) and du_t = c p
-__global__ void grad2func_finish(const cufftDoubleComplex* __restrict__ z, const double* __restrict__ p,
+template <typename CT>
+__global__ void grad2func_finish(const CT* __restrict__ z, const double* __restrict__ p,
                                  const double* __restrict__ cc, double* __restrict__ du,
                                  double* __restrict__ dut, int64_t cpts) {
     const double inv = 1.0 / (double)cpts;
     for (int64_t J = (int64_t)blockIdx.x * kT + threadIdx.x; J < cpts; J += (int64_t)gridDim.x * kT) {
-        du[J] = z[J].x * inv;
+        du[J] = (double)z[J].x * inv;
         dut[J] = cc[J] * p[J];
     }
 }
@@ -173,9 +200,10 @@ __global__ void grad2func_finish(const cufftDoubleComplex* __restrict__ z, const
 // Nyquist coefficient goes half to +nc/2 and half to -nc/2 (both halves land
 // on the same index when nf == nc); scaled by 1/cpts for the unnormalised
 // inverse transform.  Two fields (u, u_t) one after the other.
-template <int DIM>
-__global__ void interp_pad(const cufftDoubleComplex* __restrict__ cs, cufftDoubleComplex* __restrict__ fs,
-                           int64_t nc, int64_t nf, int64_t cpts, int64_t fpts) {
+template <int DIM, typename CT>
+__global__ void interp_pad(const CT* __restrict__ cs, CT* __restrict__ fs, int64_t nc, int64_t nf, int64_t cpts,
+                           int64_t fpts) {
+    using RT = real_of<CT>;
     const double scale = 1.0 / (double)cpts;
     for (int64_t idx = (int64_t)blockIdx.x * kT + threadIdx.x; idx < 2 * fpts; idx += (int64_t)gridDim.x * kT) {
         const int64_t fld = idx / fpts, jf = idx - fld * fpts;
@@ -205,40 +233,43 @@ __global__ void interp_pad(const cufftDoubleComplex* __restrict__ cs, cufftDoubl
             wgt *= wa;
             src[a] = sa;
         }
-        cufftDoubleComplex o = make_cuDoubleComplex(0.0, 0.0);
+        CT o = CT{(RT)0, (RT)0};
         if (!zero) {
-            const cufftDoubleComplex x = cs[fld * cpts + lin<DIM>(src, nc)];
-            o = make_cuDoubleComplex(x.x * wgt, x.y * wgt);
+            const CT x = cs[fld * cpts + lin<DIM>(src, nc)];
+            o = CT{(RT)(x.x * wgt), (RT)(x.y * wgt)};
         }
         fs[idx] = o;
     }
 }
 
 // out = base + real(fine field) for both fields (base may alias out)
-template <typename T>
-__global__ void interp_add(const cufftDoubleComplex* __restrict__ fs, const T* bu, const T* bv, T* ou,
+template <typename T, typename CT>
+__global__ void interp_add(const CT* __restrict__ fs, const T* bu, const T* bv, T* ou,
                            T* ov, int64_t fpts) {
     for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < fpts; j += (int64_t)gridDim.x * kT) {
-        const double a = fs[j].x, b = fs[fpts + j].x;
+        const double a = (double)fs[j].x, b = (double)fs[fpts + j].x;
         ou[j] = (T)((bu ? (double)bu[j] : 0.0) + a);
         ov[j] = (T)((bv ? (double)bv[j] : 0.0) + b);
     }
 }
 
-template <typename T>
-__global__ void to_double2(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ sa,
-                           const T* __restrict__ sb, cufftDoubleComplex* __restrict__ z, int64_t m) {
+template <typename T, typename CT>
+__global__ void to_complex2(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ sa,
+                            const T* __restrict__ sb, CT* __restrict__ z, int64_t m) {
+    using RT = real_of<CT>;
     for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
-        z[j] = make_cuDoubleComplex((double)a[j] - (sa ? (double)sa[j] : 0.0), 0.0);
-        z[m + j] = make_cuDoubleComplex((double)b[j] - (sb ? (double)sb[j] : 0.0), 0.0);
+        z[j] = CT{(RT)((double)a[j] - (sa ? (double)sa[j] : 0.0)), (RT)0};
+        z[m + j] = CT{(RT)((double)b[j] - (sb ? (double)sb[j] : 0.0)), (RT)0};
     }
 }
 
-__global__ void pair_to_complex(const double* __restrict__ a, const double* __restrict__ b,
-                                cufftDoubleComplex* __restrict__ z, int64_t m) {
+template <typename CT>
+__global__ void pair_to_complex(const double* __restrict__ a, const double* __restrict__ b, CT* __restrict__ z,
+                                int64_t m) {
+    using RT = real_of<CT>;
     for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
-        z[j] = make_cuDoubleComplex(a[j], 0.0);
-        z[m + j] = make_cuDoubleComplex(b[j], 0.0);
+        z[j] = CT{(RT)a[j], (RT)0};
+        z[m + j] = CT{(RT)b[j], (RT)0};
     }
 }
 
@@ -284,9 +315,10 @@ __global__ void reverse_cols(const double* __restrict__ E, double* __restrict__ 
         V[idx] = E[(int64_t)(h - 1 - col) * h + row];
     }
 }
-// sign of R_ii of a geqrf result (ld h), for i < r
-__global__ void diag_sign(const double* __restrict__ A, int h, int r, double* __restrict__ sg) {
-    for (int i = blockIdx.x * kT + threadIdx.x; i < r; i += gridDim.x * kT) sg[i] = A[(int64_t)i * h + i] < 0 ? -1.0 : 1.0;
+// E <- (3 I - E) / 2 (r x r): the Newton-Schulz factor
+__global__ void ns_coef(double* __restrict__ E, int r) {
+    for (int64_t idx = (int64_t)blockIdx.x * kT + threadIdx.x; idx < (int64_t)r * r; idx += (int64_t)gridDim.x * kT)
+        E[idx] = ((idx % r) == (idx / r) ? 1.5 : 0.0) - 0.5 * E[idx];
 }
 // X(:, i) = Q(:, i) sg[i]
 __global__ void scale_cols(const double* __restrict__ Q, const double* __restrict__ sg, double* __restrict__ X, int h,
@@ -309,6 +341,12 @@ struct pr_driver {
     int N = 0;
     cufftHandle plan_c1 = 0, plan_cd = 0, plan_c2 = 0, plan_f2 = 0;
     bool have_plans = false;
+    // FP32 contexts: single-precision transforms for the forward Lambda^dagger
+    // and I (the FP64 plans above stay for the adjoint)
+    bool fft32 = false;
+    cufftHandle splan_c1 = 0, splan_cd = 0, splan_c2 = 0, splan_f2 = 0;
+    float2* zc32 = nullptr;   // [max(d,2) * cpts]
+    float2* zf32 = nullptr;   // [2 * pts]
     cublasHandle_t blas = nullptr;
     cusolverDnHandle_t sol = nullptr;
     // dtype buffers
@@ -319,7 +357,7 @@ struct pr_driver {
     double* Fm = nullptr; double* Gm = nullptr;     // data matrices [rows][N], column-major
     double* dvec = nullptr; double* gvec = nullptr; // [rows]
     double* du = nullptr; double* dut = nullptr;    // coarse correction [cpts] each
-    double* zero = nullptr;                         // device scalar
+    double* zero = nullptr;                         // device scalar (then the zero-mode partials)
     cufftDoubleComplex* zc = nullptr;               // [max(d,2) * cpts]
     cufftDoubleComplex* zf = nullptr;               // [2 * pts]
     // SVD state of Alg. 1, kept factored: X = Xb WX, Y = Yb WY.  Xb, Yb
@@ -335,7 +373,8 @@ struct pr_driver {
     double *UF = nullptr, *VG = nullptr, *A1 = nullptr, *A2 = nullptr, *H = nullptr;
     double *Xh = nullptr, *YhT = nullptr, *sig = nullptr, *work = nullptr, *rwork = nullptr;
     double *F2 = nullptr, *G2 = nullptr;            // copies of F, G for the residual
-    double *E = nullptr, *tauh = nullptr, *rsign = nullptr;   // SVD through the eigenproblem of H^T H
+    double *E = nullptr, *rsign = nullptr;   // SVD through the eigenproblem of H^T H
+    double *cq = nullptr, *cq2 = nullptr;   // Cholesky QR workspace of each lane (zero-filled)
     // a second lane (stream, handles, scratch) on which G's projections,
     // deflations and QR run beside F's: those steps are latency-bound
     cudaStream_t st2 = nullptr;
@@ -374,6 +413,12 @@ void pr_driver_free(pr_ctx* ctx) {
         cufftDestroy(d->plan_cd);
         cufftDestroy(d->plan_c2);
         cufftDestroy(d->plan_f2);
+        if (d->fft32) {
+            cufftDestroy(d->splan_c1);
+            cufftDestroy(d->splan_cd);
+            cufftDestroy(d->splan_c2);
+            cufftDestroy(d->splan_f2);
+        }
     }
     if (d->blas) cublasDestroy(d->blas);
     if (d->sol) cusolverDnDestroy(d->sol);
@@ -389,8 +434,8 @@ void pr_driver_free(pr_ctx* ctx) {
     void* bufs[] = {d->vF_u, d->vF_v, d->Uc_u, d->Uc_v, d->w_u, d->w_v, d->Fm, d->Gm, d->dvec, d->gvec,
                     d->du, d->dut, d->zero, d->zc, d->zf, d->Xb, d->Yb, d->WX, d->WY, d->WXn, d->WYn,
                     d->Tb, d->vb, d->S, d->QF, d->QG, d->RF, d->RG, d->tau, d->UF, d->VG, d->A1, d->A2,
-                    d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork, d->F2, d->G2, d->info, d->E, d->tauh,
-                    d->rsign, d->Tb2, d->work2, d->tau2, d->info2};
+                    d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork, d->F2, d->G2, d->info, d->E,
+                    d->rsign, d->Tb2, d->work2, d->tau2, d->info2, d->cq, d->cq2, d->zc32, d->zf32};
     for (void* b : bufs) cudaFree(b);
     delete d;
     ctx->drv = nullptr;
@@ -446,12 +491,18 @@ pr_status driver(pr_ctx* ctx, cudaStream_t st, pr_driver** out) {
         PR_TRY_ST(alloc(ctx, (void**)&d->gvec, (size_t)d->rows * 8, "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->du, (size_t)d->cpts * 8, "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->dut, (size_t)d->cpts * 8, "driver: alloc"));
-        PR_TRY_ST(alloc(ctx, (void**)&d->zero, 8, "driver: alloc"));
+        // zero mode, kZm partials, the arrival counter
+        PR_TRY_ST(alloc(ctx, (void**)&d->zero, (size_t)(2 + kZm) * 8, "driver: alloc"));
+        PR_CUDA_TRY(ctx, cudaMemset(d->zero, 0, (size_t)(2 + kZm) * 8));
         PR_TRY_ST(alloc(ctx, (void**)&d->zc, (size_t)std::max(d->dim, 2) * d->cpts * 16, "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->zf, (size_t)2 * d->pts * 16, "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->info, sizeof(int), "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->info2, sizeof(int), "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->tau2, (size_t)d->N * 8, "driver: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&d->cq, (size_t)3 * kCqMaxCols * kCqMaxCols * 8, "driver: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&d->cq2, (size_t)3 * kCqMaxCols * kCqMaxCols * 8, "driver: alloc"));
+        PR_CUDA_TRY(ctx, cudaMemset(d->cq, 0, (size_t)3 * kCqMaxCols * kCqMaxCols * 8));
+        PR_CUDA_TRY(ctx, cudaMemset(d->cq2, 0, (size_t)3 * kCqMaxCols * kCqMaxCols * 8));
         int nn[3], nf[3];
         for (int a = 0; a < d->dim; ++a) {
             nn[a] = (int)d->nc;
@@ -462,6 +513,15 @@ pr_status driver(pr_ctx* ctx, cudaStream_t st, pr_driver** out) {
         PR_FFT(ctx, cufftPlanMany(&d->plan_c2, d->dim, nn, nullptr, 1, (int)d->cpts, nullptr, 1, (int)d->cpts, CUFFT_Z2Z, 2), "plan");
         PR_FFT(ctx, cufftPlanMany(&d->plan_f2, d->dim, nf, nullptr, 1, (int)d->pts, nullptr, 1, (int)d->pts, CUFFT_Z2Z, 2), "plan");
         d->have_plans = true;
+        if (ctx->dtype == PR_F32) {
+            PR_TRY_ST(alloc(ctx, (void**)&d->zc32, (size_t)std::max(d->dim, 2) * d->cpts * 8, "driver: alloc"));
+            PR_TRY_ST(alloc(ctx, (void**)&d->zf32, (size_t)2 * d->pts * 8, "driver: alloc"));
+            PR_FFT(ctx, cufftPlanMany(&d->splan_c1, d->dim, nn, nullptr, 1, (int)d->cpts, nullptr, 1, (int)d->cpts, CUFFT_C2C, 1), "plan");
+            PR_FFT(ctx, cufftPlanMany(&d->splan_cd, d->dim, nn, nullptr, 1, (int)d->cpts, nullptr, 1, (int)d->cpts, CUFFT_C2C, d->dim), "plan");
+            PR_FFT(ctx, cufftPlanMany(&d->splan_c2, d->dim, nn, nullptr, 1, (int)d->cpts, nullptr, 1, (int)d->cpts, CUFFT_C2C, 2), "plan");
+            PR_FFT(ctx, cufftPlanMany(&d->splan_f2, d->dim, nf, nullptr, 1, (int)d->pts, nullptr, 1, (int)d->pts, CUFFT_C2C, 2), "plan");
+            d->fft32 = true;
+        }
         d->tc = ctx->dtype == PR_F32;
         for (int i = 0; i < 6; ++i) PR_CUDA_TRY(ctx, cudaEventCreate(&d->cev[i]));
         PR_CUDA_TRY(ctx, cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming));
@@ -488,6 +548,12 @@ pr_status driver(pr_ctx* ctx, cudaStream_t st, pr_driver** out) {
     PR_FFT(ctx, cufftSetStream(d->plan_cd, st), "set stream");
     PR_FFT(ctx, cufftSetStream(d->plan_c2, st), "set stream");
     PR_FFT(ctx, cufftSetStream(d->plan_f2, st), "set stream");
+    if (d->fft32) {
+        PR_FFT(ctx, cufftSetStream(d->splan_c1, st), "set stream");
+        PR_FFT(ctx, cufftSetStream(d->splan_cd, st), "set stream");
+        PR_FFT(ctx, cufftSetStream(d->splan_c2, st), "set stream");
+        PR_FFT(ctx, cufftSetStream(d->splan_f2, st), "set stream");
+    }
     PR_BLAS(ctx, cublasSetStream(d->blas, st), "cublasSetStream");
     PR_BLAS(ctx, cusolverDnSetStream(d->sol, st), "cusolverDnSetStream");
     *out = d;
@@ -530,51 +596,88 @@ void lambda_(pr_ctx* ctx, const void* w, const void* wt, double* out, int stride
     else launch_lambda_t<double>(ctx, w, wt, out, stride, arr_n, arr_pts, sign, ns, out_ld, st);
 }
 
+// the transforms of the forward path in the precision of the context
+cufftResult fft_exec(cufftHandle p, cufftDoubleComplex* z, int dir) { return cufftExecZ2Z(p, z, z, dir); }
+cufftResult fft_exec(cufftHandle p, cufftComplex* z, int dir) { return cufftExecC2C(p, z, z, dir); }
+struct FftSet {
+    cufftHandle c1, cd, c2, f2;
+};
+template <typename CT> CT* zc_of(pr_driver* d);
+template <> double2* zc_of<double2>(pr_driver* d) { return d->zc; }
+template <> float2* zc_of<float2>(pr_driver* d) { return d->zc32; }
+template <typename CT> CT* zf_of(pr_driver* d);
+template <> double2* zf_of<double2>(pr_driver* d) { return d->zf; }
+template <> float2* zf_of<float2>(pr_driver* d) { return d->zf32; }
+template <typename CT> FftSet plans_of(pr_driver* d);
+template <> FftSet plans_of<double2>(pr_driver* d) { return {d->plan_c1, d->plan_cd, d->plan_c2, d->plan_f2}; }
+template <> FftSet plans_of<float2>(pr_driver* d) { return {d->splan_c1, d->splan_cd, d->splan_c2, d->splan_f2}; }
+
 // Lambda^dagger of gvec (rows) with zero mode *zero -> (du, dut) on the coarse grid
-pr_status reconstruct_(pr_ctx* ctx, pr_driver* d, const double* g, cudaStream_t st) {
+template <typename CT>
+pr_status reconstruct_t(pr_ctx* ctx, pr_driver* d, const double* g, cudaStream_t st) {
     const int64_t cpts = d->cpts;
-    real_to_complex<<<blocks_for(d->dim * cpts), kT, 0, st>>>(g, d->zc, d->dim * cpts);
-    PR_FFT(ctx, cufftExecZ2Z(d->plan_cd, d->zc, d->zc, CUFFT_FORWARD), "grad2func forward");
+    CT* zc = zc_of<CT>(d);
+    const FftSet P = plans_of<CT>(d);
+    real_to_complex<CT><<<blocks_for(d->dim * cpts), kT, 0, st>>>(g, zc, d->dim * cpts);
+    PR_FFT(ctx, fft_exec(P.cd, zc, CUFFT_FORWARD), "grad2func forward");
     switch (d->dim) {
-        case 1: grad2func_combine<1><<<blocks_for(cpts), kT, 0, st>>>(d->zc, d->nc, cpts, d->zero); break;
-        case 2: grad2func_combine<2><<<blocks_for(cpts), kT, 0, st>>>(d->zc, d->nc, cpts, d->zero); break;
-        default: grad2func_combine<3><<<blocks_for(cpts), kT, 0, st>>>(d->zc, d->nc, cpts, d->zero); break;
+        case 1: grad2func_combine<1, CT><<<blocks_for(cpts), kT, 0, st>>>(zc, d->nc, cpts, d->zero); break;
+        case 2: grad2func_combine<2, CT><<<blocks_for(cpts), kT, 0, st>>>(zc, d->nc, cpts, d->zero); break;
+        default: grad2func_combine<3, CT><<<blocks_for(cpts), kT, 0, st>>>(zc, d->nc, cpts, d->zero); break;
     }
-    PR_FFT(ctx, cufftExecZ2Z(d->plan_c1, d->zc, d->zc, CUFFT_INVERSE), "grad2func inverse");
-    grad2func_finish<<<blocks_for(cpts), kT, 0, st>>>(d->zc, g + (int64_t)d->dim * cpts, ctx->coarse->c64,
-                                                      d->du, d->dut, cpts);
+    PR_FFT(ctx, fft_exec(P.c1, zc, CUFFT_INVERSE), "grad2func inverse");
+    grad2func_finish<CT><<<blocks_for(cpts), kT, 0, st>>>(zc, g + (int64_t)d->dim * cpts, ctx->coarse->c64, d->du,
+                                                          d->dut, cpts);
     return PR_OK;
 }
+pr_status reconstruct_(pr_ctx* ctx, pr_driver* d, const double* g, cudaStream_t st) {
+    return d->fft32 ? reconstruct_t<float2>(ctx, d, g, st) : reconstruct_t<double2>(ctx, d, g, st);
+}
 
-// fine (u, v) = base + I(coarse fields in zc[0..2*cpts)) ; zc must hold the
-// two coarse fields as complex
-template <typename T>
+// fine (u, v) = base + I(coarse fields in the complex coarse buffer); that
+// buffer must hold the two coarse fields as complex
+template <typename T, typename CT>
 pr_status interp_t(pr_ctx* ctx, pr_driver* d, const void* bu, const void* bv, void* ou, void* ov, cudaStream_t st) {
-    PR_FFT(ctx, cufftExecZ2Z(d->plan_c2, d->zc, d->zc, CUFFT_FORWARD), "interp forward");
+    CT* zc = zc_of<CT>(d);
+    CT* zf = zf_of<CT>(d);
+    const FftSet P = plans_of<CT>(d);
+    PR_FFT(ctx, fft_exec(P.c2, zc, CUFFT_FORWARD), "interp forward");
     switch (d->dim) {
-        case 1: interp_pad<1><<<blocks_for(2 * d->pts), kT, 0, st>>>(d->zc, d->zf, d->nc, d->n, d->cpts, d->pts); break;
-        case 2: interp_pad<2><<<blocks_for(2 * d->pts), kT, 0, st>>>(d->zc, d->zf, d->nc, d->n, d->cpts, d->pts); break;
-        default: interp_pad<3><<<blocks_for(2 * d->pts), kT, 0, st>>>(d->zc, d->zf, d->nc, d->n, d->cpts, d->pts); break;
+        case 1: interp_pad<1, CT><<<blocks_for(2 * d->pts), kT, 0, st>>>(zc, zf, d->nc, d->n, d->cpts, d->pts); break;
+        case 2: interp_pad<2, CT><<<blocks_for(2 * d->pts), kT, 0, st>>>(zc, zf, d->nc, d->n, d->cpts, d->pts); break;
+        default: interp_pad<3, CT><<<blocks_for(2 * d->pts), kT, 0, st>>>(zc, zf, d->nc, d->n, d->cpts, d->pts); break;
     }
-    PR_FFT(ctx, cufftExecZ2Z(d->plan_f2, d->zf, d->zf, CUFFT_INVERSE), "interp inverse");
-    interp_add<T><<<blocks_for(d->pts), kT, 0, st>>>(d->zf, (const T*)bu, (const T*)bv, (T*)ou, (T*)ov, d->pts);
+    PR_FFT(ctx, fft_exec(P.f2, zf, CUFFT_INVERSE), "interp inverse");
+    interp_add<T, CT><<<blocks_for(d->pts), kT, 0, st>>>(zf, (const T*)bu, (const T*)bv, (T*)ou, (T*)ov, d->pts);
     return PR_OK;
 }
 pr_status interp_(pr_ctx* ctx, pr_driver* d, const void* bu, const void* bv, void* ou, void* ov, cudaStream_t st) {
-    return ctx->dtype == PR_F32 ? interp_t<float>(ctx, d, bu, bv, ou, ov, st) : interp_t<double>(ctx, d, bu, bv, ou, ov, st);
+    if (ctx->dtype == PR_F32)
+        return d->fft32 ? interp_t<float, float2>(ctx, d, bu, bv, ou, ov, st)
+                        : interp_t<float, double2>(ctx, d, bu, bv, ou, ov, st);
+    return interp_t<double, double2>(ctx, d, bu, bv, ou, ov, st);
 }
 
-// zc <- (a - sa, b - sb) for coarse dtype fields (sa/sb may be null)
+// complex coarse buffer <- (a - sa, b - sb) for coarse dtype fields (sa/sb may be null)
 void coarse_to_zc(pr_ctx* ctx, pr_driver* d, const void* a, const void* b, const void* sa, const void* sb, cudaStream_t st) {
-    if (ctx->dtype == PR_F32)
-        to_double2<float><<<blocks_for(d->cpts), kT, 0, st>>>((const float*)a, (const float*)b, (const float*)sa, (const float*)sb, d->zc, d->cpts);
-    else
-        to_double2<double><<<blocks_for(d->cpts), kT, 0, st>>>((const double*)a, (const double*)b, (const double*)sa, (const double*)sb, d->zc, d->cpts);
+    if (ctx->dtype == PR_F32) {
+        if (d->fft32)
+            to_complex2<float, float2><<<blocks_for(d->cpts), kT, 0, st>>>((const float*)a, (const float*)b, (const float*)sa, (const float*)sb, d->zc32, d->cpts);
+        else
+            to_complex2<float, double2><<<blocks_for(d->cpts), kT, 0, st>>>((const float*)a, (const float*)b, (const float*)sa, (const float*)sb, d->zc, d->cpts);
+    } else {
+        to_complex2<double, double2><<<blocks_for(d->cpts), kT, 0, st>>>((const double*)a, (const double*)b, (const double*)sa, (const double*)sb, d->zc, d->cpts);
+    }
+}
+// complex coarse buffer <- (du, dut)
+void pair_to_zc(pr_driver* d, cudaStream_t st) {
+    if (d->fft32) pair_to_complex<float2><<<blocks_for(d->cpts), kT, 0, st>>>(d->du, d->dut, d->zc32, d->cpts);
+    else pair_to_complex<double2><<<blocks_for(d->cpts), kT, 0, st>>>(d->du, d->dut, d->zc, d->cpts);
 }
 
 void zero_mode_(pr_ctx* ctx, pr_driver* d, const void* w, const void* U, cudaStream_t st) {
-    if (ctx->dtype == PR_F32) zero_mode_kernel<float><<<1, 1024, 0, st>>>((const float*)w, (const float*)U, d->cpts, d->zero);
-    else zero_mode_kernel<double><<<1, 1024, 0, st>>>((const double*)w, (const double*)U, d->cpts, d->zero);
+    if (ctx->dtype == PR_F32) zero_mode_kernel<float><<<kZm, kT, 0, st>>>((const float*)w, (const float*)U, d->cpts, d->zero);
+    else zero_mode_kernel<double><<<kZm, kT, 0, st>>>((const double*)w, (const double*)U, d->cpts, d->zero);
 }
 
 // C R of ns fine slices into coarse arrays (in place on the outputs)
@@ -630,7 +733,7 @@ pr_status ensure_capacity(pr_ctx* ctx, pr_driver* d, int need_s, int ncols, cuda
     if (h > d->hcap || !d->QF) {
         const int hc = std::max(h, d->hcap * 2);
         double** smalls[] = {&d->RF, &d->RG, &d->UF, &d->VG, &d->A1, &d->A2, &d->H, &d->Xh, &d->YhT,
-                             &d->E, &d->tauh, &d->rsign};
+                             &d->E, &d->rsign};
         for (double** p : smalls) {
             cudaFree(*p);
             *p = nullptr;
@@ -646,7 +749,6 @@ pr_status ensure_capacity(pr_ctx* ctx, pr_driver* d, int need_s, int ncols, cuda
         PR_TRY_ST(alloc(ctx, (void**)&d->Xh, (size_t)hc * hc * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->YhT, (size_t)hc * hc * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->E, (size_t)hc * hc * 8, "svd: alloc"));
-        PR_TRY_ST(alloc(ctx, (void**)&d->tauh, (size_t)hc * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->rsign, (size_t)hc * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->sig, (size_t)hc * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->rwork, (size_t)hc * 8, "svd: alloc"));
@@ -668,9 +770,14 @@ struct Lane {
     int64_t* work_len;
     double* tau;
     int* info;
+    double* cq;
 };
-Lane lane_f(pr_driver* d, cudaStream_t st) { return {st, d->blas, d->sol, d->Tb, &d->work, &d->work_len, d->tau, d->info}; }
-Lane lane_g(pr_driver* d) { return {d->st2, d->blas2, d->sol2, d->Tb2, &d->work2, &d->work2_len, d->tau2, d->info2}; }
+Lane lane_f(pr_driver* d, cudaStream_t st) {
+    return {st, d->blas, d->sol, d->Tb, &d->work, &d->work_len, d->tau, d->info, d->cq};
+}
+Lane lane_g(pr_driver* d) {
+    return {d->st2, d->blas2, d->sol2, d->Tb2, &d->work2, &d->work2_len, d->tau2, d->info2, d->cq2};
+}
 
 pr_status ensure_lane_work(pr_ctx* ctx, const Lane& L, int64_t need) {
     if (need > *L.work_len) {
@@ -697,6 +804,13 @@ pr_status ensure_work(pr_ctx* ctx, pr_driver* d, int64_t need) {
 // reduced QR of A (rows x nc, overwritten): Q in A, R (nc x nc) in Rout
 pr_status qr_(pr_ctx* ctx, pr_driver* d, const Lane& L, double* A, double* Rout, int nc) {
     const int m = (int)d->rows;
+    if (d->tc && nc <= kCqMaxCols) {
+        // FP32 contexts: Cholesky QR twice (a few FP64 passes over A instead
+        // of cuSOLVER's latency-bound Householder panels)
+        const pr_status s = cholqr2_launch(A, d->rows, nc, Rout, L.cq, L.st);
+        if (s != PR_OK) return pr_fail(ctx, s, "qr: Cholesky QR launch failed");
+        return PR_OK;
+    }
     int l1 = 0, l2 = 0;
     PR_BLAS(ctx, cusolverDnDgeqrf_bufferSize(L.sol, m, nc, A, m, &l1), "geqrf size");
     PR_BLAS(ctx, cusolverDnDorgqr_bufferSize(L.sol, m, nc, nc, A, m, L.tau, &l2), "orgqr size");
@@ -740,9 +854,9 @@ constexpr double kEigFloor = 1e-6;
 // SVD of H (h x h) for FP32 contexts from the symmetric eigenproblem of
 // H^T H (cuSOLVER syevd, several times faster than gesvd at h ~ 500):
 // H^T H = V Lambda V^T gives Y_h = V (descending order) and sigma =
-// sqrt(lambda); X_h is the orthonormal factor of the QR of H V (columns in
-// descending order, signs making R's diagonal positive), which restores
-// orthogonality that the squared spectrum loses for the small sigma.  Fills
+// sqrt(lambda); X_h is the orthonormal polar factor of H V Sigma^-1 (two
+// Newton-Schulz steps), which restores the orthogonality that the squared
+// spectrum loses for the small sigma.  Fills
 // d->Xh, d->YhT (rows 0..r-1), d->sig and `sig`; *used = false (nothing
 // written) when a kept sigma lies below kEigFloor sigma_max.
 pr_status svd_eig_(pr_ctx* ctx, pr_driver* d, int h, double tol, std::vector<double>& sig, int& r, bool& used,
@@ -773,17 +887,26 @@ pr_status svd_eig_(pr_ctx* ctx, pr_driver* d, int h, double tol, std::vector<dou
     reverse_cols<<<blocks_for((int64_t)h * r), kT, 0, st>>>(d->E, d->Xh, h, r);
     PR_BLAS(ctx, cublasDgeam(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, r, h, &one, d->Xh, h, &zero, d->Xh, r, d->YhT, h),
             "V^T");
-    // X_h = orthonormal factor of H V (Householder QR, columns in the order
-    // of decreasing sigma, signs making R's diagonal positive)
+    // X_h = the orthonormal polar factor of U0 = H V Sigma^-1.  The
+    // eigenproblem leaves U0 within ~u (sigma_1 / sigma_r)^2 <= 1e-4 of
+    // orthonormal (sigma_r >= kEigFloor sigma_1); each Newton-Schulz step
+    // X <- X (3 I - X^T X) / 2 squares that distance, so two reach FP64
+    // accuracy (four FP64 GEMMs, in place of a latency-bound Householder QR)
     PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, h, r, h, &one, d->H, h, d->Xh, h, &zero, d->E, h), "H V");
-    int l1 = 0, l2 = 0;
-    PR_BLAS(ctx, cusolverDnDgeqrf_bufferSize(d->sol, h, r, d->E, h, &l1), "geqrf size");
-    PR_BLAS(ctx, cusolverDnDorgqr_bufferSize(d->sol, h, r, r, d->E, h, d->tauh, &l2), "orgqr size");
-    PR_TRY_ST(ensure_work(ctx, d, std::max(l1, l2)));
-    PR_BLAS(ctx, cusolverDnDgeqrf(d->sol, h, r, d->E, h, d->tauh, d->work, (int)d->work_len, d->info), "geqrf");
-    diag_sign<<<blocks_for(r), kT, 0, st>>>(d->E, h, r, d->rsign);
-    PR_BLAS(ctx, cusolverDnDorgqr(d->sol, h, r, r, d->E, h, d->tauh, d->work, (int)d->work_len, d->info), "orgqr");
+    std::vector<double> inv(r);
+    for (int i = 0; i < r; ++i) inv[i] = 1.0 / sig[i];
+    cudaMemcpyAsync(d->rsign, inv.data(), (size_t)r * 8, cudaMemcpyHostToDevice, st);
     scale_cols<<<blocks_for((int64_t)h * r), kT, 0, st>>>(d->E, d->rsign, d->Xh, h, r);
+    double* nsb[2] = {d->Xh, d->H};   // H is not needed past this point
+    for (int step = 0; step < 2; ++step) {
+        double* X = nsb[step & 1];
+        double* Xn = nsb[(step + 1) & 1];
+        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, r, r, h, &one, X, h, X, h, &zero, d->E, r),
+                "X^T X");
+        ns_coef<<<blocks_for((int64_t)r * r), kT, 0, st>>>(d->E, r);
+        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, h, r, r, &one, X, h, d->E, r, &zero, Xn, h),
+                "X (3I - X^T X)/2");
+    }
     cudaMemcpyAsync(d->sig, sig.data(), (size_t)h * 8, cudaMemcpyHostToDevice, st);
     e = cudaStreamSynchronize(st);   // `sig` is a host vector the copy reads
     if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "svd_eig");
@@ -1154,7 +1277,7 @@ pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int co
                     g = d->gvec;
                 }
                 PR_TRY_ST(reconstruct_(ctx, d, g, st));
-                pair_to_complex<<<blocks_for(cpts), kT, 0, st>>>(d->du, d->dut, d->zc, cpts);
+                pair_to_zc(d, st);
             }
             const size_t vo = (size_t)(n - 1) * pts * esz;
             PR_TRY_ST(interp_(ctx, d, (char*)d->vF_u + vo, (char*)d->vF_v + vo, fu(n), fv(n), st));

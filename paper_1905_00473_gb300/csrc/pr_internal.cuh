@@ -45,6 +45,7 @@ struct pr_ctx {
     int* dev_flag = nullptr;        // device-side error flag (bounded waits)
     unsigned int* sweep_ctr = nullptr;   // grid-barrier counter of the one-launch sweep
     int one_launch = 0;             // run a supported sweep as one persistent launch (pr_set_one_launch)
+    int resident = 1;               // run slices that fit a cluster's shared memory as one launch (pr_set_resident)
     std::string err;
     // pr_profile: event pairs around launches, by kernel kind
     bool prof_on = false;
@@ -75,6 +76,15 @@ pr_status tc_gram_launch(const double* A, int64_t lda, const double* B, int64_t 
 // O (M x N, ldo) = F - A T, A (M x K, lda), T (K x N, ldt); O may equal F.
 pr_status tc_update_launch(const double* A, int64_t lda, const double* T, int64_t ldt, const double* F, int64_t ldf,
                            int64_t M, int64_t K, int N, double* O, int64_t ldo, int* flag, cudaStream_t st);
+
+// ---- tall-skinny QR (cholqr.cu) ----------------------------------------------
+// A (rows x nc, column-major, nc <= kCqMaxCols) <- Q, R (nc x nc, column-major,
+// upper) with A = Q R, by Cholesky QR twice in FP64; columns dependent on the
+// earlier ones to working accuracy get a zero row of R and a zero column of Q.
+// ws: 3 * kCqMaxCols^2 doubles, zero-filled before the first call (it is left
+// zero-filled).
+constexpr int kCqMaxCols = 64;
+pr_status cholqr2_launch(double* A, int64_t rows, int nc, double* R, double* ws, cudaStream_t st);
 
 // ---- status helpers --------------------------------------------------------
 pr_status pr_fail(pr_ctx* ctx, pr_status st, const std::string& msg);
@@ -196,6 +206,14 @@ struct pr_sweep {
 bool pr_tb2d_sweep_supported(const pr_ctx* ctx, int passes);
 // 3D FP32 temporally blocked kernel (fine_tb3d.cu): passes of 2..4 levels
 bool pr_tb3d_supported(const pr_ctx* ctx, int depth);
+
+// ---- whole slices in one cluster's shared memory (resident2d.cu) ------------
+// 2D FP32 grids up to 256^2 at block depth 8: all m + 1 kicks of each slice in
+// one launch (a cluster of 8 CTAs per slice), bit-identical to the per-pass
+// fused kernels.
+bool pr_resident2d_supported(const pr_ctx* ctx);
+pr_status pr_launch_resident2d(pr_ctx* ctx, const void* u_in, const void* v_in, void* u_out, void* v_out,
+                               int nslices, cudaStream_t st);
 pr_status pr_launch_fine_tb3d(pr_ctx* ctx, const pr_pass& p, cudaStream_t st);
 pr_status pr_launch_fine_tb2d_sweep(pr_ctx* ctx, const pr_sweep& sw, cudaStream_t st);
 pr_status pr_launch_energy(pr_ctx* ctx, const void* u, const void* v, int nslices,

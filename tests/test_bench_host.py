@@ -17,7 +17,9 @@ def test_workload_selection():
     wi = bench.workload_for("4:3", slices=8)
     assert (wi.n_fine, wi.n_slices) == (2048, 8)
     assert wi.m_f == bench.workload_for("4:3").m_f
-    for bad in ("1", "5", "4:x", "7"):
+    w5 = bench.workload_for("5")
+    assert (w5.dim, w5.n_fine, w5.n_slices) == (3, 256, 32)
+    for bad in ("1", "4:x", "7"):
         with pytest.raises((SystemExit, ValueError)):
             bench.workload_for(bad)
 
