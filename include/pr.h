@@ -340,6 +340,19 @@ pr_status pr_set_fused_columns(pr_ctx* ctx, int columns);
  * next call. */
 pr_status pr_set_one_launch(pr_ctx* ctx, int on);
 
+/* pr_set_resident -- where a 2D FP32 slice fits in the shared memory of one
+ * thread-block cluster (n = 128 or 256 at block depth 8 with four columns
+ * per thread), on != 0 makes pr_fine_all_slices propagate every slice in ONE
+ * launch, one cluster of 8 CTAs per slice holding its state on chip for all
+ * m + 1 kicks (one cluster barrier per kick); on == 0 keeps the per-pass
+ * fused launches.  Both run the same pass plan and the same operations in
+ * the same order (bit-identical results).  Default (never called): on at
+ * n = 128 (the coarse grid of the 512^2 workload, where it measured about
+ * twice as fast for one slice), off at n = 256 (eight SMs per slice measured
+ * slower than the per-pass kernels over all SMs).  Takes effect at the next
+ * call. */
+pr_status pr_set_resident(pr_ctx* ctx, int on);
+
 /* pr_debug_stall_waits -- test hook for the time-out path.  While enabled,
  * fused-kernel launches of this context expect more bulk-copy bytes than
  * they issue, so each bounded shared-memory barrier wait runs out (after
@@ -377,8 +390,9 @@ pr_status pr_energy(pr_ctx* ctx, const void* u, const void* v, int n_begin, int 
 pr_status pr_profile(pr_ctx* ctx, int on);
 
 /* pr_profile_read -- synchronise on the recorded events and report, for
- * kernel kind 0 (fused multi-level pass), 1 (single-level pass) or 2 (a whole
- * sweep in one launch, pr_set_one_launch), the number of launches recorded
+ * kernel kind 0 (fused multi-level pass), 1 (single-level pass), 2 (a whole
+ * sweep in one launch, pr_set_one_launch) or 3 (all slices resident in
+ * cluster shared memory, pr_set_resident), the number of launches recorded
  * and their summed duration in milliseconds. */
 pr_status pr_profile_read(pr_ctx* ctx, int kind, int* launches, double* total_ms);
 

@@ -74,6 +74,7 @@ _SIGNATURES = {
     "pr_batch_destroy": (None, [_P]),
     "pr_debug_stall_waits": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_set_one_launch": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pr_set_resident": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double)]),
@@ -450,5 +451,11 @@ def pr_iterate_adjoint(ctx: Context, u0, p0, K: int, corrector: int, gu_T, gv_T,
 
 
 def pr_set_one_launch(ctx: Context, on: bool) -> None:
-    """Whole sweep in one persistent launch (default) or one launch per pass."""
+    """Whole sweep in one persistent launch, or one launch per pass (the default)."""
     _check(load().pr_set_one_launch(ctx.handle, 1 if on else 0), ctx.handle)
+
+
+def pr_set_resident(ctx: Context, on: bool) -> None:
+    """Small 2D slices held in cluster shared memory for all kicks, or the
+    per-pass launches (default: on at n = 128, off at n = 256)."""
+    _check(load().pr_set_resident(ctx.handle, 1 if on else 0), ctx.handle)

@@ -27,6 +27,17 @@ constexpr int kT = 256;
 // ---------------------------------------------------------------- indexing
 template <int DIM>
 __device__ __forceinline__ void coords(int64_t j, int64_t n, int64_t* c) {
+    if (j <= 0x7fffffff && n <= 0x7fffffff) {
+        // 32-bit division: several times fewer instructions than 64-bit
+        uint32_t jj = (uint32_t)j;
+        const uint32_t nn = (uint32_t)n;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            c[a] = (int64_t)(jj % nn);
+            jj /= nn;
+        }
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         c[a] = j % n;
@@ -99,7 +110,9 @@ __global__ void lambda_kernel(const T* __restrict__ w, const T* __restrict__ wt,
             int64_t astride = 1;
             for (int b = 0; b < a; ++b) astride *= arr_n;
             for (int k = 1; k <= order_half; ++k) {
-                const int64_t cp = (c[a] + k) % nc, cm = (c[a] - k + nc) % nc;
+                int64_t cp = c[a] + k, cm = c[a] - k;   // periodic, k < nc
+                if (cp >= nc) cp -= nc;
+                if (cm < 0) cm += nc;
                 const double up = (double)ws[base + (cp * stride - f[a]) * astride];
                 const double um = (double)ws[base + (cm * stride - f[a]) * astride];
                 acc += beta.b[k - 1] * (up - um);
@@ -114,20 +127,47 @@ __global__ void lambda_kernel(const T* __restrict__ w, const T* __restrict__ wt,
     }
 }
 
-// zero mode of grad2func for the difference: sum_J (w_J - U_J).  kZm blocks
-// each reduce a fixed share in a fixed order into zbuf[1 + b]; the block that
-// finishes last adds the partials in block order into zbuf[0] and resets the
-// arrival counter (after the partials), so the sum is the same on every run.
+// kZm blocks reduce the zero mode of grad2func for the difference,
+// sum_J (w_J - U_J): each a fixed share in a fixed order into zbuf[1 + b];
+// the block that finishes last adds the partials in block order into
+// zbuf[0] and resets the arrival counter (after the partials), so the sum is
+// the same on every run.
 constexpr int kZm = 64;
-template <typename T>
-__global__ void __launch_bounds__(kT) zero_mode_kernel(const T* __restrict__ w, const T* __restrict__ U,
-                                                       int64_t cpts, double* __restrict__ zbuf) {
+
+// The serial sweep's d = Lambda w - Lambda U (coarse arrays, one slice;
+// each term rounded as lambda_kernel rounds it, then subtracted) and the
+// zero mode of w - U, in one launch of kZm blocks.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kT) lambda_diff_kernel(const T* __restrict__ w, const T* __restrict__ wt,
+                                                         const T* __restrict__ U, const T* __restrict__ Ut,
+                                                         const double* __restrict__ cc, double* __restrict__ out,
+                                                         int64_t nc, int64_t cpts, int order_half, Beta beta,
+                                                         double inv_dx, double* __restrict__ zbuf) {
     __shared__ double red[kT];
     __shared__ bool last;
-    double acc = 0.0;
-    for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < cpts; j += (int64_t)gridDim.x * kT)
-        acc += (double)w[j] - (U ? (double)U[j] : 0.0);
-    red[threadIdx.x] = acc;
+    double zacc = 0.0;
+    for (int64_t J = (int64_t)blockIdx.x * kT + threadIdx.x; J < cpts; J += (int64_t)gridDim.x * kT) {
+        int64_t c[3];
+        coords<DIM>(J, nc, c);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            int64_t astride = 1;
+            for (int b = 0; b < a; ++b) astride *= nc;
+            double aw = 0.0, au = 0.0;
+            for (int k = 1; k <= order_half; ++k) {
+                int64_t cp = c[a] + k, cm = c[a] - k;
+                if (cp >= nc) cp -= nc;
+                if (cm < 0) cm += nc;
+                const int64_t jp = J + (cp - c[a]) * astride, jm = J + (cm - c[a]) * astride;
+                aw += beta.b[k - 1] * ((double)w[jp] - (double)w[jm]);
+                au += beta.b[k - 1] * ((double)U[jp] - (double)U[jm]);
+            }
+            out[a * cpts + J] = __dsub_rn(__dmul_rn(aw, inv_dx), __dmul_rn(au, inv_dx));
+        }
+        out[DIM * cpts + J] = (double)wt[J] / cc[J] - (double)Ut[J] / cc[J];
+        zacc += (double)w[J] - (double)U[J];
+    }
+    red[threadIdx.x] = zacc;
     __syncthreads();
     for (int s = kT / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
@@ -183,15 +223,19 @@ __global__ void grad2func_combine(CT* __restrict__ z, int64_t nc, int64_t cpts, 
     }
 }
 
-// du = real(ifft(.)) (unnormalised inverse, so / cpts) and du_t = c p
+// du = real(ifft(.)) (unnormalised inverse, so / cpts) and du_t = c p, written
+// back as the two complex coarse fields that I transforms next (a thread
+// reads z[J] before it writes z[J] and z[cpts + J])
 template <typename CT>
-__global__ void grad2func_finish(const CT* __restrict__ z, const double* __restrict__ p,
-                                 const double* __restrict__ cc, double* __restrict__ du,
-                                 double* __restrict__ dut, int64_t cpts) {
+__global__ void grad2func_finish(CT* __restrict__ z, const double* __restrict__ p, const double* __restrict__ cc,
+                                 int64_t cpts) {
+    using RT = real_of<CT>;
     const double inv = 1.0 / (double)cpts;
     for (int64_t J = (int64_t)blockIdx.x * kT + threadIdx.x; J < cpts; J += (int64_t)gridDim.x * kT) {
-        du[J] = (double)z[J].x * inv;
-        dut[J] = cc[J] * p[J];
+        const double du = (double)z[J].x * inv;
+        const double dut = cc[J] * p[J];
+        z[J] = CT{(RT)du, (RT)0};
+        z[cpts + J] = CT{(RT)dut, (RT)0};
     }
 }
 
@@ -204,39 +248,39 @@ template <int DIM, typename CT>
 __global__ void interp_pad(const CT* __restrict__ cs, CT* __restrict__ fs, int64_t nc, int64_t nf, int64_t cpts,
                            int64_t fpts) {
     using RT = real_of<CT>;
-    const double scale = 1.0 / (double)cpts;
+    const RT scale = (RT)(1.0 / (double)cpts);
     for (int64_t idx = (int64_t)blockIdx.x * kT + threadIdx.x; idx < 2 * fpts; idx += (int64_t)gridDim.x * kT) {
-        const int64_t fld = idx / fpts, jf = idx - fld * fpts;
+        const int64_t fld = idx < fpts ? 0 : 1, jf = idx - fld * fpts;
         int64_t c[3];
         coords<DIM>(jf, nf, c);
-        double wgt = scale;
+        RT wgt = scale;
         int64_t src[3];
         const int64_t half = nc / 2;
         bool zero = false;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             const int64_t i = c[a];
-            double wa = 0.0;
+            RT wa = 0;
             int64_t sa = 0;
             if (nc % 2 == 0) {
-                if (i < half) { wa = 1.0; sa = i; }
-                else if (i > nf - half) { wa = 1.0; sa = i - nf + nc; }
+                if (i < half) { wa = 1; sa = i; }
+                else if (i > nf - half) { wa = 1; sa = i - nf + nc; }
                 else {
-                    if (i == half) { wa += 0.5; sa = half; }
-                    if (i == nf - half) { wa += 0.5; sa = half; }
+                    if (i == half) { wa += (RT)0.5; sa = half; }
+                    if (i == nf - half) { wa += (RT)0.5; sa = half; }
                 }
             } else {
-                if (i <= half) { wa = 1.0; sa = i; }
-                else if (i >= nf - half) { wa = 1.0; sa = i - nf + nc; }
+                if (i <= half) { wa = 1; sa = i; }
+                else if (i >= nf - half) { wa = 1; sa = i - nf + nc; }
             }
-            if (wa == 0.0) zero = true;
+            if (wa == 0) zero = true;
             wgt *= wa;
             src[a] = sa;
         }
         CT o = CT{(RT)0, (RT)0};
         if (!zero) {
             const CT x = cs[fld * cpts + lin<DIM>(src, nc)];
-            o = CT{(RT)(x.x * wgt), (RT)(x.y * wgt)};
+            o = CT{x.x * wgt, x.y * wgt};
         }
         fs[idx] = o;
     }
@@ -260,16 +304,6 @@ __global__ void to_complex2(const T* __restrict__ a, const T* __restrict__ b, co
     for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
         z[j] = CT{(RT)((double)a[j] - (sa ? (double)sa[j] : 0.0)), (RT)0};
         z[m + j] = CT{(RT)((double)b[j] - (sb ? (double)sb[j] : 0.0)), (RT)0};
-    }
-}
-
-template <typename CT>
-__global__ void pair_to_complex(const double* __restrict__ a, const double* __restrict__ b, CT* __restrict__ z,
-                                int64_t m) {
-    using RT = real_of<CT>;
-    for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
-        z[j] = CT{(RT)a[j], (RT)0};
-        z[m + j] = CT{(RT)b[j], (RT)0};
     }
 }
 
@@ -356,7 +390,6 @@ struct pr_driver {
     // FP64 buffers
     double* Fm = nullptr; double* Gm = nullptr;     // data matrices [rows][N], column-major
     double* dvec = nullptr; double* gvec = nullptr; // [rows]
-    double* du = nullptr; double* dut = nullptr;    // coarse correction [cpts] each
     double* zero = nullptr;                         // device scalar (then the zero-mode partials)
     cufftDoubleComplex* zc = nullptr;               // [max(d,2) * cpts]
     cufftDoubleComplex* zf = nullptr;               // [2 * pts]
@@ -432,7 +465,7 @@ void pr_driver_free(pr_ctx* ctx) {
     for (cudaEvent_t e : d->cev)
         if (e) cudaEventDestroy(e);
     void* bufs[] = {d->vF_u, d->vF_v, d->Uc_u, d->Uc_v, d->w_u, d->w_v, d->Fm, d->Gm, d->dvec, d->gvec,
-                    d->du, d->dut, d->zero, d->zc, d->zf, d->Xb, d->Yb, d->WX, d->WY, d->WXn, d->WYn,
+                    d->zero, d->zc, d->zf, d->Xb, d->Yb, d->WX, d->WY, d->WXn, d->WYn,
                     d->Tb, d->vb, d->S, d->QF, d->QG, d->RF, d->RG, d->tau, d->UF, d->VG, d->A1, d->A2,
                     d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork, d->F2, d->G2, d->info, d->E,
                     d->rsign, d->Tb2, d->work2, d->tau2, d->info2, d->cq, d->cq2, d->zc32, d->zf32};
@@ -489,8 +522,6 @@ pr_status driver(pr_ctx* ctx, cudaStream_t st, pr_driver** out) {
         PR_TRY_ST(alloc(ctx, (void**)&d->Gm, (size_t)d->rows * d->N * 8, "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->dvec, (size_t)d->rows * 8, "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->gvec, (size_t)d->rows * 8, "driver: alloc"));
-        PR_TRY_ST(alloc(ctx, (void**)&d->du, (size_t)d->cpts * 8, "driver: alloc"));
-        PR_TRY_ST(alloc(ctx, (void**)&d->dut, (size_t)d->cpts * 8, "driver: alloc"));
         // zero mode, kZm partials, the arrival counter
         PR_TRY_ST(alloc(ctx, (void**)&d->zero, (size_t)(2 + kZm) * 8, "driver: alloc"));
         PR_CUDA_TRY(ctx, cudaMemset(d->zero, 0, (size_t)(2 + kZm) * 8));
@@ -612,7 +643,8 @@ template <typename CT> FftSet plans_of(pr_driver* d);
 template <> FftSet plans_of<double2>(pr_driver* d) { return {d->plan_c1, d->plan_cd, d->plan_c2, d->plan_f2}; }
 template <> FftSet plans_of<float2>(pr_driver* d) { return {d->splan_c1, d->splan_cd, d->splan_c2, d->splan_f2}; }
 
-// Lambda^dagger of gvec (rows) with zero mode *zero -> (du, dut) on the coarse grid
+// Lambda^dagger of gvec (rows) with zero mode *zero -> (du, dut) on the coarse
+// grid, left in the complex coarse buffer as the two fields I interpolates
 template <typename CT>
 pr_status reconstruct_t(pr_ctx* ctx, pr_driver* d, const double* g, cudaStream_t st) {
     const int64_t cpts = d->cpts;
@@ -626,8 +658,7 @@ pr_status reconstruct_t(pr_ctx* ctx, pr_driver* d, const double* g, cudaStream_t
         default: grad2func_combine<3, CT><<<blocks_for(cpts), kT, 0, st>>>(zc, d->nc, cpts, d->zero); break;
     }
     PR_FFT(ctx, fft_exec(P.c1, zc, CUFFT_INVERSE), "grad2func inverse");
-    grad2func_finish<CT><<<blocks_for(cpts), kT, 0, st>>>(zc, g + (int64_t)d->dim * cpts, ctx->coarse->c64, d->du,
-                                                          d->dut, cpts);
+    grad2func_finish<CT><<<blocks_for(cpts), kT, 0, st>>>(zc, g + (int64_t)d->dim * cpts, ctx->coarse->c64, cpts);
     return PR_OK;
 }
 pr_status reconstruct_(pr_ctx* ctx, pr_driver* d, const double* g, cudaStream_t st) {
@@ -669,15 +700,30 @@ void coarse_to_zc(pr_ctx* ctx, pr_driver* d, const void* a, const void* b, const
         to_complex2<double, double2><<<blocks_for(d->cpts), kT, 0, st>>>((const double*)a, (const double*)b, (const double*)sa, (const double*)sb, d->zc, d->cpts);
     }
 }
-// complex coarse buffer <- (du, dut)
-void pair_to_zc(pr_driver* d, cudaStream_t st) {
-    if (d->fft32) pair_to_complex<float2><<<blocks_for(d->cpts), kT, 0, st>>>(d->du, d->dut, d->zc32, d->cpts);
-    else pair_to_complex<double2><<<blocks_for(d->cpts), kT, 0, st>>>(d->du, d->dut, d->zc, d->cpts);
-}
-
-void zero_mode_(pr_ctx* ctx, pr_driver* d, const void* w, const void* U, cudaStream_t st) {
-    if (ctx->dtype == PR_F32) zero_mode_kernel<float><<<kZm, kT, 0, st>>>((const float*)w, (const float*)U, d->cpts, d->zero);
-    else zero_mode_kernel<double><<<kZm, kT, 0, st>>>((const double*)w, (const double*)U, d->cpts, d->zero);
+// d = Lambda w - Lambda U and the zero mode of w - U (one slice, coarse arrays)
+void lambda_diff_(pr_ctx* ctx, pr_driver* d, const void* w, const void* wt, const void* U, const void* Ut,
+                  cudaStream_t st) {
+    const int h = ctx->opts.grad_order / 2;
+    const double inv_dx = 1.0 / ctx->coarse->dx;
+    const int64_t nc = d->nc, cpts = d->cpts;
+    const double* cc = ctx->coarse->c64;
+#define PR_LDIFF(T, D)                                                                                  \
+    lambda_diff_kernel<T, D><<<kZm, kT, 0, st>>>((const T*)w, (const T*)wt, (const T*)U, (const T*)Ut, cc, \
+                                                 d->dvec, nc, cpts, h, d->beta, inv_dx, d->zero)
+    if (ctx->dtype == PR_F32) {
+        switch (ctx->dim) {
+            case 1: PR_LDIFF(float, 1); break;
+            case 2: PR_LDIFF(float, 2); break;
+            default: PR_LDIFF(float, 3); break;
+        }
+    } else {
+        switch (ctx->dim) {
+            case 1: PR_LDIFF(double, 1); break;
+            case 2: PR_LDIFF(double, 2); break;
+            default: PR_LDIFF(double, 3); break;
+        }
+    }
+#undef PR_LDIFF
 }
 
 // C R of ns fine slices into coarse arrays (in place on the outputs)
@@ -1268,16 +1314,13 @@ pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int co
                 coarse_to_zc(ctx, d, d->w_u, d->w_v, Uu, Uv, st);
             } else {
                 // d = Lambda w - Lambda U_n; zero mode sum w - sum U_n (A8, by linearity)
-                lambda_(ctx, d->w_u, d->w_v, d->dvec, 1, d->nc, cpts, 1.0, 1, d->rows, st);
-                lambda_(ctx, Uu, Uv, d->dvec, 1, d->nc, cpts, -1.0, 1, d->rows, st);
-                zero_mode_(ctx, d, d->w_u, Uu, st);
+                lambda_diff_(ctx, d, d->w_u, d->w_v, Uu, Uv, st);
                 const double* g = d->dvec;
                 if (corrector == PR_CORR_PROCRUSTES) {
                     PR_TRY_ST(apply_omega(ctx, d, d->dvec, d->gvec, st));
                     g = d->gvec;
                 }
                 PR_TRY_ST(reconstruct_(ctx, d, g, st));
-                pair_to_zc(d, st);
             }
             const size_t vo = (size_t)(n - 1) * pts * esz;
             PR_TRY_ST(interp_(ctx, d, (char*)d->vF_u + vo, (char*)d->vF_v + vo, fu(n), fv(n), st));

@@ -365,6 +365,23 @@ extern "C" pr_status pr_fine_all_slices(pr_ctx* ctx, const void* u_in, const voi
         return ctx->dtype == PR_F32 ? (char*)ctx->sr[h] + (size_t)n_begin * ctx->pts * rsz : nullptr;
     };
     pr_status s = PR_OK;
+    const bool resident = ctx->resident > 0 || (ctx->resident < 0 && ctx->n <= 128);
+    if (resident && pr_resident2d_supported(ctx)) {
+        // every kick of every slice in one launch, each slice inside one cluster
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (ctx->prof_on) {
+            ea = prof_event(ctx);
+            eb = prof_event(ctx);
+            if (ea && eb) cudaEventRecord(ea, st);
+        }
+        s = pr_launch_resident2d(ctx, ui, vi, uo, vo, ns, st);
+        if (ctx->prof_on && ea && eb) {
+            cudaEventRecord(eb, st);
+            ctx->prof.push_back({3, ea, eb});
+        }
+        if (cur != ctx->device && cur >= 0) cudaSetDevice(cur);
+        return s;
+    }
     if (ctx->dtype == PR_F32 && depth == 8 && pr_tb2d_sweep_supported(ctx, passes)) {
         // every pass of the sweep in one persistent launch
         pr_sweep sw;
@@ -439,6 +456,12 @@ extern "C" pr_status pr_set_fused_columns(pr_ctx* ctx, int columns) {
     if (columns != 0 && columns != 2 && columns != 4)
         return pr_fail(ctx, PR_EINVAL, "pr_set_fused_columns: columns must be 0, 2 or 4");
     ctx->tb_cols = columns;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_set_resident(pr_ctx* ctx, int on) {
+    if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_set_resident: ctx is NULL");
+    ctx->resident = on != 0;
     return PR_OK;
 }
 

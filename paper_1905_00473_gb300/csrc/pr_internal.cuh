@@ -45,7 +45,7 @@ struct pr_ctx {
     int* dev_flag = nullptr;        // device-side error flag (bounded waits)
     unsigned int* sweep_ctr = nullptr;   // grid-barrier counter of the one-launch sweep
     int one_launch = 0;             // run a supported sweep as one persistent launch (pr_set_one_launch)
-    int resident = 1;               // run slices that fit a cluster's shared memory as one launch (pr_set_resident)
+    int resident = -1;              // slices held in one cluster's shared memory: -1 auto (n <= 128), 0 off, 1 on
     std::string err;
     // pr_profile: event pairs around launches, by kernel kind
     bool prof_on = false;

@@ -48,6 +48,7 @@ def test_fused_2d_matches_oracle(lib, n, m_f, N, medium, cols):
     ctx = P.make_ctx(w)
     from paper_1905_00473_gb300 import binding
     binding.pr_set_fused_columns(ctx, cols)
+    binding.pr_set_resident(ctx, False)   # the per-pass kernels (test_resident_gpu.py: the other path)
     assert binding.pr_info(ctx)["block_depth"] == 8
     u, v = W.slice_states(w, seed=1)
     _check_all(w, ctx, u, v)
@@ -129,6 +130,7 @@ def test_fused_2d_whole_slice_segments(lib, n, N, cols):
     ctx = P.make_ctx(w)
     from paper_1905_00473_gb300 import binding
     binding.pr_set_fused_columns(ctx, cols)
+    binding.pr_set_resident(ctx, False)
     w4 = W.custom_case(2, n, 4, 9, "f32", "inclusion")
     u4, v4 = W.slice_states(w4, seed=7)
     reps = (N + 3) // 4
@@ -159,6 +161,7 @@ def test_first_pass_and_nine_level_last_pass(lib, n, m_f):
     from paper_1905_00473_gb300 import binding
     w = W.custom_case(2, n, 3, m_f, "f32", "inclusion", seed=n + m_f)
     ctx = P.make_ctx(w)
+    binding.pr_set_resident(ctx, False)
     u, v = W.slice_states(w, seed=8)
     for one_launch in (False, True):
         binding.pr_set_one_launch(ctx, one_launch)
@@ -322,6 +325,7 @@ def test_one_launch_sweep_equals_per_pass_launches(lib, n, N, m_f):
     from paper_1905_00473_gb300 import binding
     w = W.custom_case(2, n, N, m_f, "f32", "inclusion")
     ctx = P.make_ctx(w)
+    binding.pr_set_resident(ctx, False)
     u, v = W.slice_states(w, seed=4)
     binding.pr_set_one_launch(ctx, True)
     binding.pr_profile(ctx, True)
