@@ -408,6 +408,12 @@ struct pr_driver {
     double *F2 = nullptr, *G2 = nullptr;            // copies of F, G for the residual
     double *E = nullptr, *rsign = nullptr;   // SVD through the eigenproblem of H^T H
     double *cq = nullptr, *cq2 = nullptr;   // Cholesky QR workspace of each lane (zero-filled)
+    // FP32 contexts: single-precision copies of Xb, Yb [rows][bcap] for the
+    // corrector's matrix-vector products, and their scratch
+    float *Xs = nullptr, *Ys = nullptr, *gs = nullptr;
+    double* opart = nullptr;    // [kOmJ][rows]
+    double* tpart = nullptr;    // [kOmR][kOmMaxCols]
+    unsigned* tcnt = nullptr;   // [kOmMaxCols / 2], zero-filled
     // a second lane (stream, handles, scratch) on which G's projections,
     // deflations and QR run beside F's: those steps are latency-bound
     cudaStream_t st2 = nullptr;
@@ -468,7 +474,7 @@ void pr_driver_free(pr_ctx* ctx) {
                     d->zero, d->zc, d->zf, d->Xb, d->Yb, d->WX, d->WY, d->WXn, d->WYn,
                     d->Tb, d->vb, d->S, d->QF, d->QG, d->RF, d->RG, d->tau, d->UF, d->VG, d->A1, d->A2,
                     d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork, d->F2, d->G2, d->info, d->E,
-                    d->rsign, d->Tb2, d->work2, d->tau2, d->info2, d->cq, d->cq2, d->zc32, d->zf32};
+                    d->rsign, d->Tb2, d->work2, d->tau2, d->info2, d->cq, d->cq2, d->zc32, d->zf32, d->Xs, d->Ys, d->gs, d->opart, d->tpart, d->tcnt};
     for (void* b : bufs) cudaFree(b);
     delete d;
     ctx->drv = nullptr;
@@ -534,6 +540,13 @@ pr_status driver(pr_ctx* ctx, cudaStream_t st, pr_driver** out) {
         PR_TRY_ST(alloc(ctx, (void**)&d->cq2, (size_t)3 * kCqMaxCols * kCqMaxCols * 8, "driver: alloc"));
         PR_CUDA_TRY(ctx, cudaMemset(d->cq, 0, (size_t)3 * kCqMaxCols * kCqMaxCols * 8));
         PR_CUDA_TRY(ctx, cudaMemset(d->cq2, 0, (size_t)3 * kCqMaxCols * kCqMaxCols * 8));
+        if (ctx->dtype == PR_F32) {
+            PR_TRY_ST(alloc(ctx, (void**)&d->gs, (size_t)d->rows * 4, "driver: alloc"));
+            PR_TRY_ST(alloc(ctx, (void**)&d->opart, (size_t)kOmJ * d->rows * 8, "driver: alloc"));
+            PR_TRY_ST(alloc(ctx, (void**)&d->tpart, (size_t)kOmR * kOmMaxCols * 8, "driver: alloc"));
+            PR_TRY_ST(alloc(ctx, (void**)&d->tcnt, (size_t)kOmMaxCols / 2 * 4, "driver: alloc"));
+            PR_CUDA_TRY(ctx, cudaMemset(d->tcnt, 0, (size_t)kOmMaxCols / 2 * 4));
+        }
         int nn[3], nf[3];
         for (int a = 0; a < d->dim; ++a) {
             nn[a] = (int)d->nc;
@@ -764,6 +777,19 @@ pr_status ensure_capacity(pr_ctx* ctx, pr_driver* d, int need_s, int ncols, cuda
             cudaMemcpy2D(WY, (size_t)bc * 8, d->WY, (size_t)d->bcap * 8, (size_t)d->hb * 8, d->s,
                          cudaMemcpyDeviceToDevice);
             cudaMemcpy(S, d->S, (size_t)d->s * 8, cudaMemcpyDeviceToDevice);
+        }
+        if (d->gs) {   // the FP32 copies of the bases follow the FP64 ones
+            float *Xs = nullptr, *Ys = nullptr;
+            PR_TRY_ST(alloc(ctx, (void**)&Xs, (size_t)rows * bc * 4, "svd: alloc"));
+            PR_TRY_ST(alloc(ctx, (void**)&Ys, (size_t)rows * bc * 4, "svd: alloc"));
+            if (d->s > 0) {
+                cudaMemcpy(Xs, d->Xs, (size_t)rows * d->hb * 4, cudaMemcpyDeviceToDevice);
+                cudaMemcpy(Ys, d->Ys, (size_t)rows * d->hb * 4, cudaMemcpyDeviceToDevice);
+            }
+            cudaFree(d->Xs);
+            cudaFree(d->Ys);
+            d->Xs = Xs;
+            d->Ys = Ys;
         }
         double* Tb2 = nullptr;
         PR_TRY_ST(alloc(ctx, (void**)&Tb2, (size_t)bc * d->N * 8, "svd: alloc"));
@@ -1060,6 +1086,10 @@ pr_status update_svd(pr_ctx* ctx, pr_driver* d, double* F, double* G, int nc, cu
     const int hb = d->hb, ld = d->bcap;
     cudaMemcpyAsync(d->Xb + (int64_t)hb * rows, d->QF, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(d->Yb + (int64_t)hb * rows, d->QG, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
+    if (d->Xs) {
+        omega_to_f32(d->QF, d->Xs + (int64_t)hb * rows, rows * nc, st);
+        omega_to_f32(d->QG, d->Ys + (int64_t)hb * rows, rows * nc, st);
+    }
     if (s > 0) {
         PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, hb, r, s, &one, d->WX, ld, d->Xh, h, &zero, d->WXn, ld), "WX Xh");
         PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_T, hb, r, s, &one, d->WY, ld, d->YhT, h, &zero, d->WYn, ld), "WY Yh");
@@ -1085,10 +1115,13 @@ pr_status apply_omega(pr_ctx* ctx, pr_driver* d, const double* g, double* out, c
     // X (Y^T g) = Xb (WX (WY^T (Yb^T g)))
     double* t1 = d->vb;
     double* t2 = d->vb + d->bcap;
-    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_T, (int)d->rows, d->hb, &one, d->Yb, (int)d->rows, g, 1, &zero, t1, 1), "Yb^T g");
+    const bool f32 = d->Xs && omega_f32_supported(d->rows, d->hb) == PR_OK;
+    if (f32) omega_gemv_t_f32(d->Ys, d->rows, d->hb, g, d->gs, d->tpart, d->tcnt, t1, st);
+    else PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_T, (int)d->rows, d->hb, &one, d->Yb, (int)d->rows, g, 1, &zero, t1, 1), "Yb^T g");
     PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_T, d->hb, d->s, &one, d->WY, d->bcap, t1, 1, &zero, d->rwork, 1), "WY^T");
     PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_N, d->hb, d->s, &one, d->WX, d->bcap, d->rwork, 1, &zero, t2, 1), "WX");
-    PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_N, (int)d->rows, d->hb, &one, d->Xb, (int)d->rows, t2, 1, &zero, out, 1), "Xb");
+    if (f32) omega_gemv_n_f32(d->Xs, d->rows, d->hb, t2, d->opart, out, st);
+    else PR_BLAS(ctx, cublasDgemv(d->blas, CUBLAS_OP_N, (int)d->rows, d->hb, &one, d->Xb, (int)d->rows, t2, 1, &zero, out, 1), "Xb");
     return PR_OK;
 }
 

@@ -86,6 +86,22 @@ pr_status tc_update_launch(const double* A, int64_t lda, const double* T, int64_
 constexpr int kCqMaxCols = 64;
 pr_status cholqr2_launch(double* A, int64_t rows, int nc, double* R, double* ws, cudaStream_t st);
 
+// ---- the Procrustes corrector applied with FP32 copies of the bases (omega_f32.cu)
+// Stored columns hb <= kOmMaxCols, rows % 4 == 0 (PR_EINVAL otherwise).
+constexpr int kOmJ = 8;              // column chunks of the out = Xs t2 product
+constexpr int kOmR = 4;              // row parts of the t1 = Ys^T g product
+constexpr int kOmMaxCols = 8192;
+pr_status omega_f32_supported(int64_t rows, int hb);
+void omega_to_f32(const double* a, float* b, int64_t m, cudaStream_t st);
+// t1 (hb, FP64) = Ys^T g, Ys rows x hb FP32 column-major; scratch: gs (rows
+// floats), part (kOmR * kOmMaxCols doubles), cnt (kOmMaxCols / 2 counters,
+// zero-filled before the first call; left zero-filled)
+void omega_gemv_t_f32(const float* Ys, int64_t rows, int hb, const double* g, float* gs, double* part,
+                      unsigned* cnt, double* t1, cudaStream_t st);
+// out (rows, FP64) = Xs t2; part: kOmJ * rows doubles of scratch
+void omega_gemv_n_f32(const float* Xs, int64_t rows, int hb, const double* t2, double* part, double* out,
+                      cudaStream_t st);
+
 // ---- status helpers --------------------------------------------------------
 pr_status pr_fail(pr_ctx* ctx, pr_status st, const std::string& msg);
 pr_status pr_cuda_fail(pr_ctx* ctx, cudaError_t e, const char* what);
