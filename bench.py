@@ -244,7 +244,7 @@ def workload_for(cfg: str, slices: int = 0) -> W.Workload:
     elif cfg in ("2", "3", "5"):
         w = W.CONFIGS[cfg]()
     else:
-        raise SystemExit("--config must be 2, 3, 5 or 4:<instance> for a sweep, or 4 for the batch")
+        raise SystemExit("--config must be 2, 3, 5 or 4:<instance> for a sweep, 4 for the batch or snapshot")
     if slices and slices != w.n_slices:
         m_f = w.m_f
         w.t_final = w.t_final * slices / w.n_slices
@@ -667,6 +667,56 @@ def run_ours(a) -> int:
     return 0
 
 
+# ---------------------------------------------------------------- snapshot products (Alg. 1)
+def run_snapshot(a) -> int:
+    """The two tall products of UpdateSVD on the tensor cores (split-TF32,
+    pr_snapshot_project and pr_snapshot_deflate) at the shape the 512^2
+    parareal workload reaches: rows = 3 * 128^2 Lambda features, 1024 stored
+    basis columns, 32 new columns.  Both are bound by the HBM read of the
+    FP64 basis (402 MB, above L2); one JSON line with the roofline of each."""
+    import torch
+    from paper_1905_00473_gb300 import binding
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    K, M, N = 3 * 128 * 128, 1024, 32
+    g = torch.Generator(device=dev).manual_seed(19050473)
+    A = torch.randn((M, K), dtype=torch.float64, device=dev, generator=g)   # the basis: M columns of K rows
+    B = torch.randn((N, K), dtype=torch.float64, device=dev, generator=g)
+    C = torch.empty((N, M), dtype=torch.float64, device=dev)
+    T = torch.randn((N, M), dtype=torch.float64, device=dev, generator=g)
+    O = torch.empty((N, K), dtype=torch.float64, device=dev)
+    c = torch.ones((64, 64), dtype=torch.float32, device=dev)
+    ctx = binding.pr_create(2, 64, 4, c, 0.25 / 64, 1.0 / 64, 2, 8.0 / 64)
+    peak, peak_src = measured_peak()
+    out = {"metric": "snapshot_products_hbm", "impl": "ours", "unit": "GB/s", "data": "synthetic",
+           "config": {"workload": "UpdateSVD products, rows 49152 x basis 1024 x new 32 (FP64 operands)"},
+           "steps": a.steps, "warmup": a.warmup}
+    calls = {
+        "project": (lambda: binding.pr_snapshot_project(ctx, A, B, C), (M * K + N * K) * 8 + M * N * 8),
+        # O = F - A T with the same basis A (1024 columns of 49152 rows), F = B
+        "deflate": (lambda: binding.pr_snapshot_deflate(ctx, A, T, B, O), (M * K + 2 * N * K) * 8 + M * N * 8),
+    }
+    for name, (fn, nbytes) in calls.items():
+        for _ in range(a.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "algorithmic_bytes": nbytes,
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                  "frac": gbs / peak, "peak_source": peak_src},
+                     "tflops_split_tf32": 4 * 2 * M * N * K / (ms * 1e-3) / 1e12}
+    binding.pr_check(ctx)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -674,7 +724,8 @@ def main(argv=None) -> int:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="3",
-                    help="2, 3, 5: the sweep workloads; 4: the uneven batch; 4:<i>: instance i of the batch alone")
+                    help="2, 3, 5: the sweep workloads; 4: the uneven batch; 4:<i>: instance i of the batch "
+                         "alone; snapshot: the tensor-core products of UpdateSVD")
     ap.add_argument("--block-depth", type=int, default=0, help="0 = library default")
     ap.add_argument("--columns", type=int, default=0, choices=[0, 2, 4],
                     help="fused-kernel columns per thread (0 = library default)")
@@ -696,6 +747,8 @@ def main(argv=None) -> int:
         return run_reference(a)
     if a.config == "4":
         return run_batch(a)
+    if a.config == "snapshot":
+        return run_snapshot(a)
     return run_ours(a)
 
 

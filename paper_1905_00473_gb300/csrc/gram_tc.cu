@@ -23,8 +23,9 @@
 // chunk's FP64 values, split them and store hi and lo into 128-byte-swizzled
 // K-major tiles (two stages), then thread 0 issues 4 K-steps x 4 MMAs and
 // commits them to the stage's mbarrier, which the threads wait on before
-// they overwrite that stage.  The loads of the next chunk are issued before
-// that wait, so HBM traffic overlaps the MMAs.  Every wait is bounded.
+// they overwrite that stage.  Two chunks are held in registers: once chunk
+// c is in shared memory the loads of chunk c + 2 are issued, so two chunks'
+// HBM reads overlap the MMAs and the next split.  Every wait is bounded.
 //
 // The split-K gram sums its CTAs' partials with FP64 atomic adds into C,
 // which the launcher clears first.
@@ -285,19 +286,21 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramArgs g) {
     // MMA batches committed per stage (stage s has been used issued_s times)
     uint32_t issued0 = 0, issued1 = 0;
 
-    Chunk<NB> x;
-    if (c_begin < c_end) load_chunk<MODE, NB>(g, m0, c_begin * kKc, x);
-    for (int64_t c = c_begin; c < c_end; ++c) {
-        const int s = (int)((c - c_begin) % kStages);
+    // Two chunks in registers: chunk c + 2 is requested as soon as chunk c is
+    // in shared memory, so two chunks' loads are in flight while the MMAs and
+    // the next chunk's split run (chunk c uses stage (c - c_begin) % 2).
+    Chunk<NB> x0, x1;
+    if (c_begin < c_end) load_chunk<MODE, NB>(g, m0, c_begin * kKc, x0);
+    if (c_begin + 1 < c_end) load_chunk<MODE, NB>(g, m0, (c_begin + 1) * kKc, x1);
+    auto step = [&](int64_t c, Chunk<NB>& x, int s, uint32_t& used) -> bool {
         unsigned char* st = sm + s * S::stage;
         // the stage's previous MMAs must be done before it is overwritten
-        const uint32_t used = s == 0 ? issued0 : issued1;
         if (used > 0 && ok) {
             if (!bar_wait(&bars[s], (used - 1) & 1u, g.wait_ns)) ok = false;
         }
         if (!__syncthreads_and(ok)) {
             ok = false;
-            break;
+            return false;
         }
         store_chunk<MODE, NB>(x, st);
         __syncthreads();
@@ -316,9 +319,13 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramArgs g) {
             }
             mma_commit(&bars[s]);
         }
-        if (s == 0) ++issued0; else ++issued1;
-        // the next chunk's loads overlap these MMAs and the next stage wait
-        if (c + 1 < c_end) load_chunk<MODE, NB>(g, m0, (c + 1) * kKc, x);
+        ++used;
+        if (c + 2 < c_end) load_chunk<MODE, NB>(g, m0, (c + 2) * kKc, x);
+        return true;
+    };
+    for (int64_t c = c_begin; c < c_end; c += 2) {
+        if (!step(c, x0, 0, issued0)) break;
+        if (c + 1 < c_end && !step(c + 1, x1, 1, issued1)) break;
     }
     // all MMAs done: wait for the last commit of every stage used
     bool done = true;
@@ -408,8 +415,11 @@ pr_status tc_gram_launch(const double* A, int64_t lda, const double* B, int64_t 
         }
         return PR_OK;
     }
-    for (int n = 0; n < N; ++n) {
-        cudaError_t e = cudaMemsetAsync(C + (int64_t)n * ldc, 0, (size_t)M * sizeof(double), st);
+    {
+        // one clearing call for the N columns (the split-K CTAs add into C)
+        cudaError_t e = ldc == M ? cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(double), st)
+                                 : cudaMemset2DAsync(C, (size_t)ldc * sizeof(double), 0, (size_t)M * sizeof(double),
+                                                     (size_t)N, st);
         if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "gram_tc: clear");
     }
     if (K <= 0) return PR_OK;
