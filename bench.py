@@ -732,7 +732,7 @@ def main(argv=None) -> int:
     ap.add_argument("--slices", type=int, default=0,
                     help="propagate only this many slices (smaller profiling runs; 0 = all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--instances", type=int, default=8, help="--config 4: instances in the batch")
+    ap.add_argument("--instances", type=int, default=48, help="--config 4: instances in the batch (all 48)")
     ap.add_argument("--no-parareal", action="store_true",
                     help="skip the parareal time-to-1e-4 measurement")
     ap.add_argument("--one-launch", choices=["on", "off"], default="off",
