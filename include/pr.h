@@ -91,7 +91,9 @@ typedef struct pr_ctx pr_ctx;
  *
  * Checks the CFL condition of the Verlet/central-difference pair,
  * max c * dt * sqrt(dim) / dx <= 1, on both grids (PR_EINVAL if violated).
- * Synchronises the device (it reads max c back).
+ * Reads c back on a private stream ordered after the work already queued on
+ * the legacy default stream (write c there, or synchronise the stream that
+ * wrote it, before the call); no other stream is waited for.
  */
 pr_status pr_create(const pr_grid* grid, const void* c_dev, double dt_f, double dt_c, int N,
                     double T, const pr_options* opts, pr_ctx** out);
@@ -137,6 +139,28 @@ enum { PR_CORR_PROCRUSTES = 0, PR_CORR_OMEGA1 = 1, PR_CORR_PLAIN = 2 };
  * run by the same kernels as F. */
 pr_status pr_coarse_sweep(pr_ctx* ctx, const void* u, const void* v, void* U_out, void* V_out,
                           int n_begin, int n_end, void* stream);
+
+/* pr_serial_sweep -- the serial corrected sweep of Alg. 3 (the serial
+ * update of one iteration; the coarse sweep in its corrected, serial form),
+ * so that a caller can compose Alg. 3 from pr_fine_all_slices,
+ * pr_coarse_sweep, pr_procrustes_correct and this call.  For n = 1..N:
+ *   w = C R u_{n-1}  (this call's own, on the new states),
+ *   u_n = F_n + I(theta(w) - theta(U_n))
+ * with theta of the corrector (PR_CORR_*; PR_CORR_PROCRUSTES applies the
+ * Omega = X Y^T that pr_procrustes_correct has built in this context, and an
+ * empty one, rank 0, gives a zero correction).
+ *  Fu, Fv    F u^k_{n-1} for n = 1..N: fine states [N][n^d] (dtype), read.
+ *  Uu, Uv    C R u^k_{n-1} for n = 1..N: coarse states [N][(n/ratio)^d]
+ *            (dtype), read (pr_coarse_sweep writes them).
+ *  u_slices, v_slices  [N+1][n^d] (dtype): slice 0 holds u^{k+1}_0 on entry
+ *            (read); slices 1..N receive u^{k+1}_n.  No input may overlap
+ *            slices 1..N of the outputs.
+ * Requires a context with a coarse grid (PR_EINVAL otherwise).  FP32
+ * contexts apply Omega with single-precision copies of the stored bases
+ * (FP32-accurate, as the state is).  Returns after queuing the work and
+ * reading the coarse propagation's device error flag (synchronises). */
+pr_status pr_serial_sweep(pr_ctx* ctx, int corrector, const void* Fu, const void* Fv, const void* Uu,
+                          const void* Uv, void* u_slices, void* v_slices, void* stream);
 
 /* pr_iterate -- the proposed method, Alg. 3, for up to K iterations.
  *  u0, p0      initial state [n^d] (dtype, device).

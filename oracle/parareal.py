@@ -98,6 +98,32 @@ class IterationRecord:
     Y: Optional[np.ndarray] = None
 
 
+def serial_sweep(P: Problem, start, v, Uc, X, Y):
+    """The serial corrected sweep of Alg. 3: from u^{k+1}_0 = start, for
+    n = 1..N, w = C R u^{k+1}_{n-1} and u^{k+1}_n = v_n + I(theta w - theta U_n),
+    with v_n = F u^k_{n-1}, U_n = C R u^k_{n-1} and theta of P.corrector
+    (Procrustes: I Lambda^dagger X Y^T Lambda).  Returns u^{k+1}_0..N."""
+    new = [start]
+    for n in range(1, P.n_slices + 1):
+        w, wt = C(P, *R(P, *new[n - 1]))
+        Un, Unt = Uc[n - 1]
+        if P.corrector == "plain":
+            du, dut = w - Un, wt - Unt
+        else:
+            lw, lU = Lam(P, w, wt), Lam(P, Un, Unt)
+            if P.corrector == "procrustes":
+                qp = procrustes.apply_corrector(X, Y, lw)
+                qpt = procrustes.apply_corrector(X, Y, lU)
+            else:   # Omega = 1
+                qp, qpt = lw, lU
+            q1, p = transfer.reconstruct(qp, float(np.sum(w)), P.c_coarse)
+            q1t, pt = transfer.reconstruct(qpt, float(np.sum(Un)), P.c_coarse)
+            du, dut = q1 - q1t, p - pt
+        cu, cut = I(P, du, dut)
+        new.append((v[n - 1][0] + cu, v[n - 1][1] + cut))
+    return new
+
+
 def iterate(P: Problem, u0: np.ndarray, p0: np.ndarray, K: int):
     """K iterations of Alg. 3 from the initial guess; returns the records."""
     u = initial_guess(P, u0, p0)
@@ -114,26 +140,7 @@ def iterate(P: Problem, u0: np.ndarray, p0: np.ndarray, K: int):
             Gm = np.stack([Lam(P, *Un) for Un in Uc], axis=1)
             X, S, Y = procrustes.update_svd(X, S, Y, Fm, Gm, P.tol)
             residual = float(np.linalg.norm(Fm - X @ (Y.T @ Gm)) / np.linalg.norm(Fm))
-        # serial corrected sweep
-        new = [u[0]]
-        for n in range(1, P.n_slices + 1):
-            w, wt = C(P, *R(P, *new[n - 1]))
-            Un, Unt = Uc[n - 1]
-            if P.corrector == "plain":
-                du, dut = w - Un, wt - Unt
-            else:
-                lw, lU = Lam(P, w, wt), Lam(P, Un, Unt)
-                if P.corrector == "procrustes":
-                    qp = procrustes.apply_corrector(X, Y, lw)
-                    qpt = procrustes.apply_corrector(X, Y, lU)
-                else:   # Omega = 1
-                    qp, qpt = lw, lU
-                q1, p = transfer.reconstruct(qp, float(np.sum(w)), P.c_coarse)
-                q1t, pt = transfer.reconstruct(qpt, float(np.sum(Un)), P.c_coarse)
-                du, dut = q1 - q1t, p - pt
-            cu, cut = I(P, du, dut)
-            new.append((v[n - 1][0] + cu, v[n - 1][1] + cut))
-        u = new
+        u = serial_sweep(P, u[0], v, Uc, X, Y)
         records.append(IterationRecord(k, 0 if S is None else int(S.size), residual, u, X, Y))
     return records
 

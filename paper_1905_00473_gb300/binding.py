@@ -75,6 +75,7 @@ _SIGNATURES = {
     "pr_debug_stall_waits": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_set_one_launch": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_set_resident": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pr_serial_sweep": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double)]),
@@ -276,6 +277,20 @@ def pr_coarse_sweep(ctx: Context, u, v, U_out, V_out, n_begin: int = 0,
     st = load().pr_coarse_sweep(ctx.handle, ctx._arr(u, "u"), ctx._arr(v, "v"),
                                 ctx._arr(U_out, "U_out", cc), ctx._arr(V_out, "V_out", cc),
                                 n_begin, n_end, ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, ctx.handle)
+
+
+def pr_serial_sweep(ctx: Context, corrector: int, Fu, Fv, Uu, Uv, u_slices, v_slices, stream=None) -> None:
+    """Serial corrected sweep of Alg. 3: slices 1..N of u_slices/v_slices from
+    slice 0, the fine values F u^k_{n-1} (Fu, Fv [N, ...]) and the coarse
+    values C R u^k_{n-1} (Uu, Uv [N, coarse ...])."""
+    pts = ctx.n ** ctx.dim
+    cc = ctx.N * ctx.n_coarse ** ctx.dim
+    st = load().pr_serial_sweep(ctx.handle, corrector, ctx._arr(Fu, "Fu", ctx.N * pts),
+                                ctx._arr(Fv, "Fv", ctx.N * pts), ctx._arr(Uu, "Uu", cc), ctx._arr(Uv, "Uv", cc),
+                                ctx._arr(u_slices, "u_slices", (ctx.N + 1) * pts),
+                                ctx._arr(v_slices, "v_slices", (ctx.N + 1) * pts),
+                                ctypes.c_void_p(_stream_ptr(stream)))
     _check(st, ctx.handle)
 
 

@@ -1214,11 +1214,44 @@ struct IterRecord {
     std::vector<double*> wx, wy;   // hb_k x s_k, column-major (ld hb_k)
 };
 
+pr_status serial_sweep_(pr_ctx* ctx, pr_driver* d, int corrector, const void* Fu, const void* Fv, const void* Uc_u,
+                        const void* Uc_v, void* u, void* v, cudaStream_t st);
 pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector, double tol_err,
                       const void* u_ref, const void* v_ref, void* u_slices, void* v_slices, double* err_hist,
                       double* resid_hist, int* rank_hist, int* k_done, cudaStream_t st, IterRecord* rec);
 
 }  // namespace
+
+extern "C" pr_status pr_serial_sweep(pr_ctx* ctx, int corrector, const void* Fu, const void* Fv, const void* Uu,
+                                     const void* Uv, void* u_slices, void* v_slices, void* stream) {
+    if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_serial_sweep: ctx is NULL");
+    if (!Fu || !Fv || !Uu || !Uv || !u_slices || !v_slices)
+        return pr_fail(ctx, PR_EINVAL, "pr_serial_sweep: NULL array");
+    if (corrector < PR_CORR_PROCRUSTES || corrector > PR_CORR_PLAIN)
+        return pr_fail(ctx, PR_EINVAL, "pr_serial_sweep: unknown corrector");
+    if (!ctx->coarse) return pr_fail(ctx, PR_EINVAL, "pr_serial_sweep: context has no coarse grid");
+    {
+        const size_t esz = ctx->dtype == PR_F32 ? 4 : 8;
+        const size_t fb = (size_t)ctx->N * ctx->pts * esz, cb = (size_t)ctx->N * ctx->coarse->pts * esz;
+        const char* lo[2] = {(const char*)u_slices + ctx->pts * esz, (const char*)v_slices + ctx->pts * esz};
+        const char* in[4] = {(const char*)Fu, (const char*)Fv, (const char*)Uu, (const char*)Uv};
+        const size_t ib[4] = {fb, fb, cb, cb};
+        auto hit = [](const char* a, size_t na, const char* b, size_t nb) { return a < b + nb && b < a + na; };
+        if (hit(lo[0], fb, lo[1], fb)) return pr_fail(ctx, PR_EINVAL, "pr_serial_sweep: u_slices and v_slices overlap");
+        for (int i = 0; i < 4; ++i)
+            for (int o = 0; o < 2; ++o)
+                if (hit(in[i], ib[i], lo[o], fb))
+                    return pr_fail(ctx, PR_EINVAL, "pr_serial_sweep: an input overlaps output slices 1..N");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    pr_driver* d = nullptr;
+    PR_TRY_ST(driver(ctx, st, &d));
+    PR_TRY_ST(serial_sweep_(ctx, d, corrector, Fu, Fv, Uu, Uv, u_slices, v_slices, st));
+    PR_TRY_ST(pr_take_flag(ctx->coarse, ctx, st, "pr_serial_sweep (coarse propagation)"));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "pr_serial_sweep");
+    return PR_OK;
+}
 
 extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector,
                                 double tol_err, const void* u_ref, const void* v_ref, void* u_slices,
@@ -1229,6 +1262,39 @@ extern "C" pr_status pr_iterate(pr_ctx* ctx, const void* u0, const void* p0, int
 }
 
 namespace {
+
+// The serial corrected sweep of Alg. 3: for n = 1..N, w = C R u_{n-1} and
+// u_n = F_n + I(correction), the correction w - U_n (plain), or Lambda^dagger
+// of Lambda w - Lambda U_n (Omega = 1) or of Omega (Lambda w - Lambda U_n)
+// (Procrustes), with the zero mode sum w - sum U_n (A8, by linearity).  F
+// ([N][pts]) holds F u^k_{n-1}, U ([N][cpts]) C R u^k_{n-1}; u, v ([N+1][pts])
+// hold u^{k+1}_0 in slice 0 and receive slices 1..N.
+pr_status serial_sweep_(pr_ctx* ctx, pr_driver* d, int corrector, const void* Fu, const void* Fv, const void* Uc_u,
+                        const void* Uc_v, void* u, void* v, cudaStream_t st) {
+    const size_t esz = ctx->dtype == PR_F32 ? 4 : 8;
+    const int64_t pts = ctx->pts, cpts = d->cpts;
+    auto fu = [&](int n) { return (char*)u + (size_t)n * pts * esz; };
+    auto fv = [&](int n) { return (char*)v + (size_t)n * pts * esz; };
+    for (int n = 1; n <= ctx->N; ++n) {
+        PR_TRY_ST(coarse_of(ctx, fu(n - 1), fv(n - 1), d->w_u, d->w_v, 1, st));
+        const void* Uu = (const char*)Uc_u + (size_t)(n - 1) * cpts * esz;
+        const void* Uv = (const char*)Uc_v + (size_t)(n - 1) * cpts * esz;
+        if (corrector == PR_CORR_PLAIN) {
+            coarse_to_zc(ctx, d, d->w_u, d->w_v, Uu, Uv, st);
+        } else {
+            lambda_diff_(ctx, d, d->w_u, d->w_v, Uu, Uv, st);
+            const double* g = d->dvec;
+            if (corrector == PR_CORR_PROCRUSTES) {
+                PR_TRY_ST(apply_omega(ctx, d, d->dvec, d->gvec, st));
+                g = d->gvec;
+            }
+            PR_TRY_ST(reconstruct_(ctx, d, g, st));
+        }
+        const size_t vo = (size_t)(n - 1) * pts * esz;
+        PR_TRY_ST(interp_(ctx, d, (const char*)Fu + vo, (const char*)Fv + vo, fu(n), fv(n), st));
+    }
+    return PR_OK;
+}
 
 pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int corrector, double tol_err,
                       const void* u_ref, const void* v_ref, void* u_slices, void* v_slices, double* err_hist,
@@ -1267,7 +1333,6 @@ pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int co
     char* vs = (char*)v_slices;
     auto fu = [&](int n) { return us + (size_t)n * pts * esz; };
     auto fv = [&](int n) { return vs + (size_t)n * pts * esz; };
-    auto cu = [&](void* base, int n) { return (char*)base + (size_t)n * cpts * esz; };
 
     // Alg. 3 initialisation: u^1_0 = [u0, p0], u^1_n = I C R u^1_{n-1}
     cudaEventRecord(d->ev[0], st);
@@ -1339,25 +1404,7 @@ pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int co
         }
         cudaEventRecord(d->ev[2], st);
         // serial corrected sweep; u^{k+1}_0 = u^k_0 stays
-        for (int n = 1; n <= N; ++n) {
-            PR_TRY_ST(coarse_of(ctx, fu(n - 1), fv(n - 1), d->w_u, d->w_v, 1, st));
-            const void* Uu = cu(d->Uc_u, n - 1);
-            const void* Uv = cu(d->Uc_v, n - 1);
-            if (corrector == PR_CORR_PLAIN) {
-                coarse_to_zc(ctx, d, d->w_u, d->w_v, Uu, Uv, st);
-            } else {
-                // d = Lambda w - Lambda U_n; zero mode sum w - sum U_n (A8, by linearity)
-                lambda_diff_(ctx, d, d->w_u, d->w_v, Uu, Uv, st);
-                const double* g = d->dvec;
-                if (corrector == PR_CORR_PROCRUSTES) {
-                    PR_TRY_ST(apply_omega(ctx, d, d->dvec, d->gvec, st));
-                    g = d->gvec;
-                }
-                PR_TRY_ST(reconstruct_(ctx, d, g, st));
-            }
-            const size_t vo = (size_t)(n - 1) * pts * esz;
-            PR_TRY_ST(interp_(ctx, d, (char*)d->vF_u + vo, (char*)d->vF_v + vo, fu(n), fv(n), st));
-        }
+        PR_TRY_ST(serial_sweep_(ctx, d, corrector, d->vF_u, d->vF_v, d->Uc_u, d->Uc_v, us, vs, st));
         cudaEventRecord(d->ev[3], st);
         record_states(k + 1);
         PR_TRY_ST(add_phase(1, 0, 1));

@@ -152,8 +152,20 @@ extern "C" pr_status pr_create(const pr_grid* grid, const void* c_dev, double dt
             cudaGetLastError();
             return pr_fail(nullptr, PR_EINVAL, "pr_create: c must be a device pointer");
         }
+        // on a private non-blocking stream ordered after the work already
+        // queued on the legacy default stream, so that no other stream of
+        // the device is waited for
         std::vector<char> raw(pts * esz);
-        cudaError_t e = cudaMemcpy(raw.data(), c_dev, pts * esz, cudaMemcpyDeviceToHost);
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ce = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ce, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ce, (cudaStream_t)0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ce, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(raw.data(), c_dev, pts * esz, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (ce) cudaEventDestroy(ce);
+        if (cs) cudaStreamDestroy(cs);
         if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "pr_create: copy c");
         for (int64_t i = 0; i < pts; ++i)
             c[i] = o.dtype == PR_F32 ? (double)((const float*)raw.data())[i] : ((const double*)raw.data())[i];
