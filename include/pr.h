@@ -101,6 +101,25 @@ pr_status pr_create(const pr_grid* grid, const void* c_dev, double dt_f, double 
 /* pr_destroy -- free the context and all device memory it owns (NULL is a no-op). */
 void pr_destroy(pr_ctx* ctx);
 
+/* Caller allocator (ownership: the context owns kappa, the pass scratch,
+ * snapshot stores, SVD factors and workspaces; these can come from the
+ * caller's pool, e.g. PyTorch's caching allocator, instead of cudaMalloc).
+ *  alloc(bytes, device, user)  returns device memory of at least `bytes`
+ *                              bytes on `device` (the current device), or
+ *                              NULL on failure (reported as PR_ECUDA);
+ *  release(ptr, user)          gives it back.
+ * pr_set_allocator installs the pair process-wide for contexts created
+ * afterwards; each context keeps the pair it was created with, so a context
+ * and its frees always use the same allocator.  Both NULL restores
+ * cudaMalloc / cudaFree; exactly one NULL is PR_EINVAL.  Not synchronised
+ * with concurrent pr_create calls.  Before it hands memory back the library
+ * synchronises the device (cudaFree does the same implicitly), so released
+ * memory is idle.  Workspaces that cuFFT, cuBLAS and cuSOLVER allocate
+ * inside their own handles and plans are not routed through the pair. */
+typedef void* (*pr_alloc_fn)(size_t bytes, int device, void* user);
+typedef void (*pr_release_fn)(void* ptr, void* user);
+pr_status pr_set_allocator(pr_alloc_fn alloc, pr_release_fn release, void* user);
+
 /* pr_last_error -- message of the last failing call on ctx (never NULL).
  * With ctx == NULL returns the last error of pr_create on this thread. */
 const char* pr_last_error(const pr_ctx* ctx);

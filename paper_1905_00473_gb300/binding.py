@@ -40,7 +40,11 @@ class pr_options(ctypes.Structure):
 
 
 _P = ctypes.c_void_p
+# pr_set_allocator's callbacks: alloc(bytes, device, user) -> pointer, release(ptr, user)
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+_RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 _SIGNATURES = {
+    "pr_set_allocator": (ctypes.c_int, [_ALLOC_FN, _RELEASE_FN, _P]),
     "pr_create": (ctypes.c_int, [ctypes.POINTER(pr_grid), _P, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_int, ctypes.c_double, ctypes.POINTER(pr_options),
                                  ctypes.POINTER(_P)]),
@@ -127,6 +131,35 @@ def _check(status: int, ctx_ptr) -> None:
     if status != 0:
         msg = load().pr_last_error(ctx_ptr)
         raise PrError(status, msg.decode() if msg else "")
+
+
+# every callback pair ever installed: contexts keep calling the pair they were
+# created with (until pr_destroy), so none may be collected
+_allocator_refs = []
+
+
+def pr_set_allocator(alloc=None, release=None) -> None:
+    """Device memory of contexts created from now on: alloc(nbytes, device)
+    returns a device address (int; 0 on failure) and release(address) gives
+    it back; both None restores cudaMalloc.  Contexts keep the pair they were
+    created with."""
+    if alloc is None and release is None:
+        _check(load().pr_set_allocator(_ALLOC_FN(), _RELEASE_FN(), None), None)   # NULL pointers
+        return
+    if alloc is None or release is None:
+        raise ValueError("pr_set_allocator: give both functions or neither")
+    ca = _ALLOC_FN(lambda nbytes, dev, user: alloc(int(nbytes), int(dev)) or None)
+    cr = _RELEASE_FN(lambda ptr, user: release(int(ptr)))
+    _allocator_refs.append((ca, cr))
+    _check(load().pr_set_allocator(ca, cr, None), None)
+
+
+def use_torch_allocator() -> None:
+    """Contexts created from now on take their device memory from PyTorch's
+    caching allocator (on the current stream of the device)."""
+    import torch
+    pr_set_allocator(lambda nbytes, dev: torch.cuda.caching_allocator_alloc(nbytes, device=dev),
+                     lambda ptr: torch.cuda.caching_allocator_delete(ptr))
 
 
 class Context:

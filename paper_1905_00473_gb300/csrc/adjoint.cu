@@ -172,10 +172,10 @@ pr_status run(pr_ctx* ctx, const T* u0, const T* p0, const T* guT, const T* gvT,
     // workspace: checkpoints (N+1) x (u, v), trace (m+1), v, 4 adjoint fields, FP64 gk
     const size_t need = (size_t)(2 * (N + 1) + (m + 1) + 1 + 4) * fb + (size_t)pts * 8;
     if (need > ctx->adj_bytes) {
-        cudaFree(ctx->adj_ws);
+        pr_dev_free(ctx, ctx->adj_ws);
         ctx->adj_ws = nullptr;
         ctx->adj_bytes = 0;
-        cudaError_t e = cudaMalloc(&ctx->adj_ws, need);
+        cudaError_t e = pr_dev_malloc(ctx, &ctx->adj_ws, need);
         if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "pr_adjoint: workspace");
         ctx->adj_bytes = need;
     }
@@ -266,10 +266,10 @@ pr_status slice_adjoint_t(pr_ctx* c, const T* u_in, const T* v_in, T* lu, T* lv,
     if (need > c->sadj_bytes) {
         cudaError_t e = cudaStreamSynchronize(st);   // the old workspace may still be in use
         if (e != cudaSuccess) return pr_cuda_fail(c, e, "slice adjoint: synchronize");
-        cudaFree(c->sadj_ws);
+        pr_dev_free(c, c->sadj_ws);
         c->sadj_ws = nullptr;
         c->sadj_bytes = 0;
-        e = cudaMalloc(&c->sadj_ws, need);
+        e = pr_dev_malloc(c, &c->sadj_ws, need);
         if (e != cudaSuccess) return pr_cuda_fail(c, e, "slice adjoint: workspace");
         c->sadj_bytes = need;
     }

@@ -70,10 +70,10 @@ pr_status pr_launch_energy(pr_ctx* ctx, const void* u, const void* v, int ns, do
     if (nb < 1) nb = 1;
     const int64_t need = (int64_t)ns * nb + ns;
     if (need > ctx->partials_len) {
-        cudaFree(ctx->partials);
+        pr_dev_free(ctx, ctx->partials);
         ctx->partials = nullptr;
         ctx->partials_len = 0;
-        PR_CUDA_TRY(ctx, cudaMalloc((void**)&ctx->partials, need * sizeof(double)));
+        PR_CUDA_TRY(ctx, pr_dev_malloc(ctx, (void**)&ctx->partials, need * sizeof(double)));
         ctx->partials_len = need;
     }
     double* part = ctx->partials;

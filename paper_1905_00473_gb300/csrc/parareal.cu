@@ -475,7 +475,7 @@ void pr_driver_free(pr_ctx* ctx) {
                     d->Tb, d->vb, d->S, d->QF, d->QG, d->RF, d->RG, d->tau, d->UF, d->VG, d->A1, d->A2,
                     d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork, d->F2, d->G2, d->info, d->E,
                     d->rsign, d->Tb2, d->work2, d->tau2, d->info2, d->cq, d->cq2, d->zc32, d->zf32, d->Xs, d->Ys, d->gs, d->opart, d->tpart, d->tcnt};
-    for (void* b : bufs) cudaFree(b);
+    for (void* b : bufs) pr_dev_free(ctx, b);
     delete d;
     ctx->drv = nullptr;
 }
@@ -497,7 +497,7 @@ pr_status blas_fail(pr_ctx* ctx, int r, const char* what) {
 #define PR_BLAS(ctx, x, what) do { int r_ = (int)(x); if (r_ != 0) return blas_fail(ctx, r_, what); } while (0)
 
 pr_status alloc(pr_ctx* ctx, void** p, size_t bytes, const char* what) {
-    cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 16);
+    cudaError_t e = pr_dev_malloc(ctx, p, bytes > 0 ? bytes : 16);
     if (e != cudaSuccess) return pr_cuda_fail(ctx, e, what);
     return PR_OK;
 }
@@ -786,17 +786,17 @@ pr_status ensure_capacity(pr_ctx* ctx, pr_driver* d, int need_s, int ncols, cuda
                 cudaMemcpy(Xs, d->Xs, (size_t)rows * d->hb * 4, cudaMemcpyDeviceToDevice);
                 cudaMemcpy(Ys, d->Ys, (size_t)rows * d->hb * 4, cudaMemcpyDeviceToDevice);
             }
-            cudaFree(d->Xs);
-            cudaFree(d->Ys);
+            pr_dev_free(ctx, d->Xs);
+            pr_dev_free(ctx, d->Ys);
             d->Xs = Xs;
             d->Ys = Ys;
         }
         double* Tb2 = nullptr;
         PR_TRY_ST(alloc(ctx, (void**)&Tb2, (size_t)bc * d->N * 8, "svd: alloc"));
-        cudaFree(d->Tb2);
+        pr_dev_free(ctx, d->Tb2);
         d->Tb2 = Tb2;
         double** olds[] = {&d->Xb, &d->Yb, &d->WX, &d->WY, &d->WXn, &d->WYn, &d->Tb, &d->vb, &d->S};
-        for (double** o : olds) cudaFree(*o);
+        for (double** o : olds) pr_dev_free(ctx, *o);
         d->Xb = Xb; d->Yb = Yb; d->WX = WX; d->WY = WY; d->WXn = WXn; d->WYn = WYn;
         d->Tb = Tb; d->vb = vb; d->S = S;
         d->bcap = bc;
@@ -807,10 +807,10 @@ pr_status ensure_capacity(pr_ctx* ctx, pr_driver* d, int need_s, int ncols, cuda
         double** smalls[] = {&d->RF, &d->RG, &d->UF, &d->VG, &d->A1, &d->A2, &d->H, &d->Xh, &d->YhT,
                              &d->E, &d->rsign};
         for (double** p : smalls) {
-            cudaFree(*p);
+            pr_dev_free(ctx, *p);
             *p = nullptr;
         }
-        cudaFree(d->sig); cudaFree(d->tau); cudaFree(d->QF); cudaFree(d->QG); cudaFree(d->rwork);
+        for (double* q : {d->sig, d->tau, d->QF, d->QG, d->rwork}) pr_dev_free(ctx, q);
         PR_TRY_ST(alloc(ctx, (void**)&d->RF, (size_t)ncols * ncols * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->RG, (size_t)ncols * ncols * 8, "svd: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->UF, (size_t)hc * ncols * 8, "svd: alloc"));
@@ -855,7 +855,7 @@ pr_status ensure_lane_work(pr_ctx* ctx, const Lane& L, int64_t need) {
     if (need > *L.work_len) {
         cudaError_t e = cudaStreamSynchronize(L.st);
         if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "svd: synchronize");
-        cudaFree(*L.work);
+        pr_dev_free(ctx, *L.work);
         *L.work = nullptr;
         PR_TRY_ST(alloc(ctx, (void**)L.work, (size_t)need * 8, "svd: alloc work"));
         *L.work_len = need;
@@ -865,7 +865,7 @@ pr_status ensure_lane_work(pr_ctx* ctx, const Lane& L, int64_t need) {
 
 pr_status ensure_work(pr_ctx* ctx, pr_driver* d, int64_t need) {
     if (need > d->work_len) {
-        cudaFree(d->work);
+        pr_dev_free(ctx, d->work);
         d->work = nullptr;
         PR_TRY_ST(alloc(ctx, (void**)&d->work, (size_t)need * 8, "svd: alloc work"));
         d->work_len = need;
@@ -1752,7 +1752,7 @@ pr_status adjoint_run(pr_ctx* ctx, pr_driver* d, const IterRecord& rec, int K, i
     pr_status status = adj_alloc<T>(ctx, w, N, pts, cpts, d->rows);
     auto release = [&]() {
         cudaStreamSynchronize(st);
-        for (void* p : w.all) cudaFree(p);
+        for (void* p : w.all) pr_dev_free(ctx, p);
     };
     if (status != PR_OK) {
         release();
@@ -1909,17 +1909,17 @@ extern "C" pr_status pr_iterate_adjoint(pr_ctx* ctx, const void* u0, const void*
     void* vs = nullptr;
     auto cleanup = [&]() {
         cudaStreamSynchronize(st);
-        cudaFree(rec.hu);
-        cudaFree(rec.hv);
-        cudaFree(us);
-        cudaFree(vs);
-        for (double* p : rec.wx) cudaFree(p);
-        for (double* p : rec.wy) cudaFree(p);
+        pr_dev_free(ctx, rec.hu);
+        pr_dev_free(ctx, rec.hv);
+        pr_dev_free(ctx, us);
+        pr_dev_free(ctx, vs);
+        for (double* p : rec.wx) pr_dev_free(ctx, p);
+        for (double* p : rec.wy) pr_dev_free(ctx, p);
     };
     pr_status s = PR_OK;
-    if (cudaMalloc((void**)&rec.hu, slab * (K + 1)) != cudaSuccess ||
-        cudaMalloc((void**)&rec.hv, slab * (K + 1)) != cudaSuccess || cudaMalloc(&us, slab) != cudaSuccess ||
-        cudaMalloc(&vs, slab) != cudaSuccess) {
+    if (pr_dev_malloc(ctx, (void**)&rec.hu, slab * (K + 1)) != cudaSuccess ||
+        pr_dev_malloc(ctx, (void**)&rec.hv, slab * (K + 1)) != cudaSuccess || pr_dev_malloc(ctx, &us, slab) != cudaSuccess ||
+        pr_dev_malloc(ctx, &vs, slab) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
         return pr_fail(ctx, PR_ENOMEM, "pr_iterate_adjoint: state history");

@@ -27,6 +27,45 @@ extern "C" const char* pr_last_error(const pr_ctx* ctx) {
     return ctx ? ctx->err.c_str() : g_create_err.c_str();
 }
 
+static pr_alloc_fn g_alloc = nullptr;
+static pr_release_fn g_release = nullptr;
+static void* g_alloc_user = nullptr;
+
+void pr_current_allocator(pr_alloc_fn* a, pr_release_fn* r, void** user) {
+    *a = g_alloc;
+    *r = g_release;
+    *user = g_alloc_user;
+}
+
+cudaError_t pr_dev_malloc(const pr_ctx* ctx, void** p, size_t bytes) {
+    if (ctx && ctx->ualloc) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        *p = ctx->ualloc(bytes, dev, ctx->uarg);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+void pr_dev_free(const pr_ctx* ctx, void* p) {
+    if (!p) return;
+    if (ctx && ctx->urelease) {
+        cudaDeviceSynchronize();
+        ctx->urelease(p, ctx->uarg);
+        return;
+    }
+    cudaFree(p);
+}
+
+extern "C" pr_status pr_set_allocator(pr_alloc_fn alloc, pr_release_fn release, void* user) {
+    if ((alloc == nullptr) != (release == nullptr))
+        return pr_fail(nullptr, PR_EINVAL, "pr_set_allocator: give both functions or neither");
+    g_alloc = alloc;
+    g_release = release;
+    g_alloc_user = alloc ? user : nullptr;
+    return PR_OK;
+}
+
 static void free_all(pr_ctx* c) {
     pr_driver_free(c);
     if (c->coarse) {
@@ -34,22 +73,22 @@ static void free_all(pr_ctx* c) {
         delete c->coarse;
         c->coarse = nullptr;
     }
-    cudaFree(c->c64);
-    cudaFree(c->adj_ws);
+    pr_dev_free(c, c->c64);
+    pr_dev_free(c, c->adj_ws);
     c->adj_ws = nullptr;
-    cudaFree(c->sadj_ws);
+    pr_dev_free(c, c->sadj_ws);
     c->sadj_ws = nullptr;
-    cudaFree(c->kappa);
-    cudaFree(c->kappa_il);
-    cudaFree(c->cinv2);
+    pr_dev_free(c, c->kappa);
+    pr_dev_free(c, c->kappa_il);
+    pr_dev_free(c, c->cinv2);
     for (int h = 0; h < 2; ++h) {
-        cudaFree(c->su[h]);
-        cudaFree(c->sv[h]);
-        cudaFree(c->sr[h]);
+        pr_dev_free(c, c->su[h]);
+        pr_dev_free(c, c->sv[h]);
+        pr_dev_free(c, c->sr[h]);
     }
-    cudaFree(c->partials);
-    cudaFree(c->dev_flag);
-    cudaFree(c->sweep_ctr);
+    pr_dev_free(c, c->partials);
+    pr_dev_free(c, c->dev_flag);
+    pr_dev_free(c, c->sweep_ctr);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
 }
@@ -236,6 +275,7 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
     double cmax = 0;
     for (int64_t i = 0; i < pts; ++i) cmax = std::max(cmax, c[i]);
     pr_ctx* ctx = new pr_ctx();
+    pr_current_allocator(&ctx->ualloc, &ctx->urelease, &ctx->uarg);
     cudaGetDevice(&ctx->device);
     ctx->dim = dim;
     ctx->n = n;
@@ -272,9 +312,9 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
         return s;
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&ctx->kappa, pts * esz)) != cudaSuccess) return fail(e, "pr_create: alloc kappa");
-    if ((e = cudaMalloc((void**)&ctx->cinv2, pts * 8)) != cudaSuccess) return fail(e, "pr_create: alloc cinv2");
-    if ((e = cudaMalloc((void**)&ctx->c64, pts * 8)) != cudaSuccess) return fail(e, "pr_create: alloc c");
+    if ((e = pr_dev_malloc(ctx, &ctx->kappa, pts * esz)) != cudaSuccess) return fail(e, "pr_create: alloc kappa");
+    if ((e = pr_dev_malloc(ctx, (void**)&ctx->cinv2, pts * 8)) != cudaSuccess) return fail(e, "pr_create: alloc cinv2");
+    if ((e = pr_dev_malloc(ctx, (void**)&ctx->c64, pts * 8)) != cudaSuccess) return fail(e, "pr_create: alloc c");
     if ((e = cudaMemcpy(ctx->kappa, kap.data(), pts * esz, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "pr_create: upload kappa");
     if ((e = cudaMemcpy(ctx->cinv2, cinv2.data(), pts * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -288,7 +328,7 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
             il[4 * j] = kf[2 * j];
             il[4 * j + 1] = kf[2 * j + 1];
         }
-        if ((e = cudaMalloc((void**)&ctx->kappa_il, pts * 8)) != cudaSuccess) return fail(e, "pr_create: alloc kappa pairs");
+        if ((e = pr_dev_malloc(ctx, (void**)&ctx->kappa_il, pts * 8)) != cudaSuccess) return fail(e, "pr_create: alloc kappa pairs");
         if ((e = cudaMemcpy(ctx->kappa_il, il.data(), pts * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
             return fail(e, "pr_create: upload kappa pairs");
     }
@@ -299,14 +339,14 @@ pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt
     ctx->resid_bytes = o.dtype != PR_F32 ? 0
                        : (pr_tb2d_supported(ctx, 8) || pr_tb2d_supported(ctx, 4) || pr_tb3d_supported(ctx, 4)) ? 2 : 1;
     for (int h = 0; h < 2; ++h) {
-        if ((e = cudaMalloc(&ctx->su[h], state * esz)) != cudaSuccess) return fail(e, "pr_create: alloc scratch u");
-        if ((e = cudaMalloc(&ctx->sv[h], state * esz)) != cudaSuccess) return fail(e, "pr_create: alloc scratch v");
-        if (ctx->resid_bytes && (e = cudaMalloc(&ctx->sr[h], state * ctx->resid_bytes)) != cudaSuccess)
+        if ((e = pr_dev_malloc(ctx, &ctx->su[h], state * esz)) != cudaSuccess) return fail(e, "pr_create: alloc scratch u");
+        if ((e = pr_dev_malloc(ctx, &ctx->sv[h], state * esz)) != cudaSuccess) return fail(e, "pr_create: alloc scratch v");
+        if (ctx->resid_bytes && (e = pr_dev_malloc(ctx, &ctx->sr[h], state * ctx->resid_bytes)) != cudaSuccess)
             return fail(e, "pr_create: alloc scratch residual");
     }
-    if ((e = cudaMalloc((void**)&ctx->dev_flag, sizeof(int))) != cudaSuccess) return fail(e, "pr_create: alloc flag");
+    if ((e = pr_dev_malloc(ctx, (void**)&ctx->dev_flag, sizeof(int))) != cudaSuccess) return fail(e, "pr_create: alloc flag");
     if ((e = cudaMemset(ctx->dev_flag, 0, sizeof(int))) != cudaSuccess) return fail(e, "pr_create: clear flag");
-    if ((e = cudaMalloc((void**)&ctx->sweep_ctr, sizeof(unsigned int))) != cudaSuccess)
+    if ((e = pr_dev_malloc(ctx, (void**)&ctx->sweep_ctr, sizeof(unsigned int))) != cudaSuccess)
         return fail(e, "pr_create: alloc sweep counter");
     *out = ctx;
     return PR_OK;

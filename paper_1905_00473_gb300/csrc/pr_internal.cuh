@@ -45,6 +45,9 @@ struct pr_ctx {
     int* dev_flag = nullptr;        // device-side error flag (bounded waits)
     unsigned int* sweep_ctr = nullptr;   // grid-barrier counter of the one-launch sweep
     int one_launch = 0;             // run a supported sweep as one persistent launch (pr_set_one_launch)
+    pr_alloc_fn ualloc = nullptr;     // the caller allocator at creation (pr_set_allocator), or cudaMalloc
+    pr_release_fn urelease = nullptr;
+    void* uarg = nullptr;
     int resident = -1;              // slices held in one cluster's shared memory: -1 auto (n <= 128), 0 off, 1 on
     std::string err;
     // pr_profile: event pairs around launches, by kernel kind
@@ -54,6 +57,15 @@ struct pr_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
 };
+
+// ---- device memory owned by a context ------------------------------------------
+// Through the caller allocator the context was created with, else cudaMalloc /
+// cudaFree.  pr_dev_free synchronises the device before it hands memory to a
+// caller allocator (cudaFree does so implicitly); NULL is a no-op.
+cudaError_t pr_dev_malloc(const pr_ctx* ctx, void** p, size_t bytes);
+void pr_dev_free(const pr_ctx* ctx, void* p);
+// the process-wide pair that pr_create records into new contexts
+void pr_current_allocator(pr_alloc_fn* a, pr_release_fn* r, void** user);
 
 // ---- context construction / driver teardown ---------------------------------
 pr_status pr_build_ctx(int dim, int64_t n, int ratio, int N, double T, double dt, int m,

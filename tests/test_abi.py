@@ -69,3 +69,14 @@ def test_noalloc_binding_rejects_unequal_axes_before_any_launch():
         binding.pr_fine_all_slices_noalloc(torch.ones((8, 8)), 1e-3, 4, torch.zeros((2, 8, 4)),
                                            torch.zeros((2, 8, 4)), torch.zeros((2, 8, 4)),
                                            torch.zeros((2, 8, 4)))
+
+
+def test_allocator_setter_is_host_only(libpath):
+    """pr_set_allocator installs and clears the callback pair without a device
+    (no CUDA call); one function without the other is PR_EINVAL."""
+    binding.pr_set_allocator(lambda nbytes, dev: 0, lambda ptr: None)
+    binding.pr_set_allocator(None, None)
+    with pytest.raises(ValueError):
+        binding.pr_set_allocator(lambda nbytes, dev: 0, None)
+    lib = binding.load()
+    assert lib.pr_set_allocator(binding._ALLOC_FN(lambda n, d, u: None), binding._RELEASE_FN(), None) != 0
