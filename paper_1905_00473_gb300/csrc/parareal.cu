@@ -408,6 +408,7 @@ struct pr_driver {
     double *F2 = nullptr, *G2 = nullptr;            // copies of F, G for the residual
     double *E = nullptr, *rsign = nullptr;   // SVD through the eigenproblem of H^T H
     double *cq = nullptr, *cq2 = nullptr;   // Cholesky QR workspace of each lane (zero-filled)
+    double* rnorm = nullptr;                // ||F||, ||F - Omega G|| of the last residual
     // FP32 contexts: single-precision copies of Xb, Yb [rows][bcap] for the
     // corrector's matrix-vector products, and their scratch
     float *Xs = nullptr, *Ys = nullptr, *gs = nullptr;
@@ -474,7 +475,7 @@ void pr_driver_free(pr_ctx* ctx) {
                     d->zero, d->zc, d->zf, d->Xb, d->Yb, d->WX, d->WY, d->WXn, d->WYn,
                     d->Tb, d->vb, d->S, d->QF, d->QG, d->RF, d->RG, d->tau, d->UF, d->VG, d->A1, d->A2,
                     d->H, d->Xh, d->YhT, d->sig, d->work, d->rwork, d->F2, d->G2, d->info, d->E,
-                    d->rsign, d->Tb2, d->work2, d->tau2, d->info2, d->cq, d->cq2, d->zc32, d->zf32, d->Xs, d->Ys, d->gs, d->opart, d->tpart, d->tcnt};
+                    d->rsign, d->Tb2, d->work2, d->tau2, d->info2, d->cq, d->cq2, d->rnorm, d->zc32, d->zf32, d->Xs, d->Ys, d->gs, d->opart, d->tpart, d->tcnt};
     for (void* b : bufs) pr_dev_free(ctx, b);
     delete d;
     ctx->drv = nullptr;
@@ -538,6 +539,7 @@ pr_status driver(pr_ctx* ctx, cudaStream_t st, pr_driver** out) {
         PR_TRY_ST(alloc(ctx, (void**)&d->tau2, (size_t)d->N * 8, "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->cq, (size_t)3 * kCqMaxCols * kCqMaxCols * 8, "driver: alloc"));
         PR_TRY_ST(alloc(ctx, (void**)&d->cq2, (size_t)3 * kCqMaxCols * kCqMaxCols * 8, "driver: alloc"));
+        PR_TRY_ST(alloc(ctx, (void**)&d->rnorm, 2 * 8, "driver: alloc"));
         PR_CUDA_TRY(ctx, cudaMemset(d->cq, 0, (size_t)3 * kCqMaxCols * kCqMaxCols * 8));
         PR_CUDA_TRY(ctx, cudaMemset(d->cq2, 0, (size_t)3 * kCqMaxCols * kCqMaxCols * 8));
         if (ctx->dtype == PR_F32) {
@@ -1125,20 +1127,25 @@ pr_status apply_omega(pr_ctx* ctx, pr_driver* d, const double* g, double* out, c
     return PR_OK;
 }
 
-// ||F - X Y^T G||_F / ||F||_F for the current data (F, G unmodified copies in Fm/Gm)
-pr_status residual_(pr_ctx* ctx, pr_driver* d, const double* F, const double* G, int nc, double* res,
-                    cudaStream_t st) {
+// ||F - X Y^T G||_F and ||F||_F for the current data (F, G unmodified copies)
+// into d->rnorm[1], d->rnorm[0], on lane g: a diagnostic that runs beside the
+// serial sweep (which touches none of QF, UF, the bases or lane g's scratch);
+// the next UpdateSVD is ordered after it through ev_join.
+pr_status residual_(pr_ctx* ctx, pr_driver* d, const double* F, const double* G, int nc) {
     const int64_t rows = d->rows;
-    double nf = 0, nr = 0;
-    PR_BLAS(ctx, cublasDnrm2(d->blas, (int)(rows * nc), F, 1, &nf), "nrm2");
+    const Lane L = lane_g(d);
+    PR_BLAS(ctx, cublasSetPointerMode(L.blas, CUBLAS_POINTER_MODE_DEVICE), "pointer mode");
+    PR_BLAS(ctx, cublasDnrm2(L.blas, (int)(rows * nc), F, 1, d->rnorm), "nrm2");
     // QF (rows x nc) <- F - X (Y^T G): reuse QF/UF scratch (UF has >= s*nc)
-    cudaMemcpyAsync(d->QF, F, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(d->QF, F, (size_t)rows * nc * 8, cudaMemcpyDeviceToDevice, L.st);
     if (d->s > 0) {
-        PR_TRY_ST(project_(ctx, d, lane_f(d, st), d->Yb, d->WY, G, nc, d->UF));
-        PR_TRY_ST(subtract_(ctx, d, lane_f(d, st), d->Xb, d->WX, d->UF, nc, d->QF));
+        PR_BLAS(ctx, cublasSetPointerMode(L.blas, CUBLAS_POINTER_MODE_HOST), "pointer mode");
+        PR_TRY_ST(project_(ctx, d, L, d->Yb, d->WY, G, nc, d->UF));
+        PR_TRY_ST(subtract_(ctx, d, L, d->Xb, d->WX, d->UF, nc, d->QF));
+        PR_BLAS(ctx, cublasSetPointerMode(L.blas, CUBLAS_POINTER_MODE_DEVICE), "pointer mode");
     }
-    PR_BLAS(ctx, cublasDnrm2(d->blas, (int)(rows * nc), d->QF, 1, &nr), "nrm2");
-    *res = nf > 0 ? nr / nf : 0.0;
+    PR_BLAS(ctx, cublasDnrm2(L.blas, (int)(rows * nc), d->QF, 1, d->rnorm + 1), "nrm2");
+    PR_BLAS(ctx, cublasSetPointerMode(L.blas, CUBLAS_POINTER_MODE_HOST), "pointer mode");
     return PR_OK;
 }
 
@@ -1361,6 +1368,7 @@ pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int co
         PR_TRY_ST(coarse_of(ctx, fu(0), fv(0), d->Uc_u, d->Uc_v, N, st));
         cudaEventRecord(d->ev[1], st);
         double res = 0.0;
+        bool resid_pending = false;
         if (corrector == PR_CORR_PROCRUSTES) {
             // F = [Lambda R v_n], G = [Lambda U_n]; UpdateSVD (Alg. 1)
             lambda_(ctx, d->vF_u, d->vF_v, d->Fm, ctx->ratio, ctx->n, pts, 1.0, N, d->rows, st);
@@ -1373,16 +1381,13 @@ pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int co
             cudaMemcpyAsync(d->F2, d->Fm, (size_t)d->rows * N * 8, cudaMemcpyDeviceToDevice, st);
             cudaMemcpyAsync(d->G2, d->Gm, (size_t)d->rows * N * 8, cudaMemcpyDeviceToDevice, st);
             PR_TRY_ST(update_svd(ctx, d, d->Fm, d->Gm, N, st));
-            PR_TRY_ST(residual_(ctx, d, d->F2, d->G2, N, &res, st));
-            cudaEventRecord(d->cev[5], st);
-            {
-                PR_CUDA_TRY(ctx, cudaEventSynchronize(d->cev[5]));
-                for (int i = 0; i < 5; ++i) {
-                    float ms = 0.0f;
-                    PR_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, d->cev[i], d->cev[i + 1]));
-                    d->corr_ms[i] += ms;
-                }
-            }
+            // the residual diagnostic on lane g, beside the serial sweep
+            cudaEventRecord(d->ev_fork, st);
+            cudaStreamWaitEvent(d->st2, d->ev_fork, 0);
+            PR_TRY_ST(residual_(ctx, d, d->F2, d->G2, N));
+            cudaEventRecord(d->cev[5], d->st2);
+            cudaEventRecord(d->ev_join, d->st2);
+            resid_pending = true;
             if (rec) {
                 // freeze Omega^k: the W blocks (hb x s, ld bcap) as they are now
                 double* wx = nullptr;
@@ -1406,6 +1411,20 @@ pr_status iterate_run(pr_ctx* ctx, const void* u0, const void* p0, int K, int co
         // serial corrected sweep; u^{k+1}_0 = u^k_0 stays
         PR_TRY_ST(serial_sweep_(ctx, d, corrector, d->vF_u, d->vF_v, d->Uc_u, d->Uc_v, us, vs, st));
         cudaEventRecord(d->ev[3], st);
+        if (resid_pending) {
+            // the next iteration's UpdateSVD reuses the residual's scratch
+            cudaStreamWaitEvent(st, d->ev_join, 0);
+            double nrm[2] = {0.0, 0.0};
+            PR_CUDA_TRY(ctx, cudaEventSynchronize(d->cev[5]));
+            PR_CUDA_TRY(ctx, cudaMemcpy(nrm, d->rnorm, sizeof nrm, cudaMemcpyDeviceToHost));
+            res = nrm[0] > 0 ? nrm[1] / nrm[0] : 0.0;
+            for (int i = 0; i < 5; ++i) {
+                float ms = 0.0f;
+                PR_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, d->cev[i], d->cev[i + 1]));
+                d->corr_ms[i] += ms;
+            }
+            resid_pending = false;
+        }
         record_states(k + 1);
         PR_TRY_ST(add_phase(1, 0, 1));
         PR_TRY_ST(add_phase(2, 1, 2));
