@@ -17,9 +17,11 @@
 // TF32's 2^-11.  Partial sums leave tensor memory in FP32 and are combined in
 // FP64.
 //
-// Kernel shape.  128 threads per CTA; thread t owns tile row t (the M = 128
-// accumulator rows map onto the 128 tensor-memory lanes, warp w reads lanes
-// 32w..32w+31).  K advances in chunks of 32 elements: the threads load the
+// Kernel shape.  256 threads per CTA, two CTAs per SM (16 warps to hide the
+// split's latency); the M = 128 accumulator rows map onto the 128
+// tensor-memory lanes, and in the epilogue warps w and w + 4 read lanes
+// 32w..32w+31, each half of the columns.  K advances in chunks of 32
+// elements: the threads load the
 // chunk's FP64 values, split them and store hi and lo into 128-byte-swizzled
 // K-major tiles (two stages), then thread 0 issues 4 K-steps x 4 MMAs and
 // commits them to the stage's mbarrier, which the threads wait on before
@@ -37,7 +39,7 @@
 
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;   // two threads per tile row (kM rows)
 constexpr int kM = 128;          // accumulator rows per CTA (tensor-memory lanes)
 constexpr int kKc = 32;          // K elements per chunk: 32 tf32 = 128 bytes per row
 constexpr int kStages = 2;       // smem stages (the loop below tracks exactly two)
@@ -168,17 +170,18 @@ struct GramArgs {
     uint64_t wait_ns;
 };
 
-// One K chunk in registers: thread t's share of the A tile (8 groups of 4
-// elements) and of the B tile (NB/16 groups).  MODE 0 (gram): A rows are
-// contiguous in K, thread t takes group t % 8 of rows t/8 + 16 j.  MODE 1
-// (update): A columns are contiguous in M, thread t takes row t and the 8
-// groups of 4 columns, each element a load coalesced across the warp.  B
-// (NB rows, contiguous in K) in both modes: item i = t + 128 j is group i % 8
-// of row i / 8.  Elements outside the matrices are zero.
+// One K chunk in registers: thread t's share of the A tile (4 groups of 4
+// elements) and of the B tile (NB/32 groups).  MODE 0 (gram): A rows are
+// contiguous in K, thread t takes group t % 8 of rows t/8 + 32 j.  MODE 1
+// (update): A columns are contiguous in M, thread t takes row t % 128 and the
+// groups 4 (t / 128) .. 4 (t / 128) + 3 of 4 columns, each element a load
+// coalesced across the warp.  B (NB rows, contiguous in K) in both modes:
+// item i = t + 256 j is group i % 8 of row i / 8.  Elements outside the
+// matrices are zero.
 template <int NB>
 struct Chunk {
-    double a[8][4];
-    double b[NB / 16][4];
+    double a[4][4];
+    double b[NB / 32][4];
 };
 
 template <int MODE, int NB>
@@ -186,8 +189,8 @@ __device__ __forceinline__ void load_chunk(const GramArgs& g, int64_t m0, int64_
     const int t = threadIdx.x;
     if (MODE == 0) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int64_t gm = m0 + t / 8 + 16 * j, gk = k0 + 4 * (t % 8);
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gm = m0 + t / 8 + 32 * j, gk = k0 + 4 * (t % 8);
             const double* src = g.A + gm * g.lda + gk;
             if (gm < g.M && gk + 3 < g.K && (((uintptr_t)src) & 15) == 0) {
                 const double2 p0 = __ldcs((const double2*)src), p1 = __ldcs((const double2*)src + 1);
@@ -198,17 +201,17 @@ __device__ __forceinline__ void load_chunk(const GramArgs& g, int64_t m0, int64_
             }
         }
     } else {
-        const int64_t gm = m0 + t;
+        const int64_t gm = m0 + t % kM;
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int64_t gk = k0 + 4 * c + e;
+                const int64_t gk = k0 + 4 * (4 * (t / kM) + c) + e;
                 x.a[c][e] = (gm < g.M && gk < g.K) ? __ldcs(g.A + gk * g.lda + gm) : 0.0;
             }
     }
 #pragma unroll
-    for (int j = 0; j < NB / 16; ++j) {
+    for (int j = 0; j < NB / 32; ++j) {
         const int i = t + kThreads * j;
         const int n = i / 8;
         const int64_t gk = k0 + 4 * (i % 8);
@@ -228,9 +231,9 @@ __device__ __forceinline__ void store_chunk(const Chunk<NB>& x, unsigned char* s
     unsigned char* bhi = st + 2 * S::a_bytes;
     unsigned char* blo = bhi + S::b_bytes;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int m = MODE == 0 ? t / 8 + 16 * j : t;
-        const int c = MODE == 0 ? t % 8 : j;
+    for (int j = 0; j < 4; ++j) {
+        const int m = MODE == 0 ? t / 8 + 32 * j : t % kM;
+        const int c = MODE == 0 ? t % 8 : 4 * (t / kM) + j;
         uint4 h, l;
         split_tf32(x.a[j][0], h.x, l.x); split_tf32(x.a[j][1], h.y, l.y);
         split_tf32(x.a[j][2], h.z, l.z); split_tf32(x.a[j][3], h.w, l.w);
@@ -238,7 +241,7 @@ __device__ __forceinline__ void store_chunk(const Chunk<NB>& x, unsigned char* s
         *(uint4*)(alo + sw128(m, c)) = l;
     }
 #pragma unroll
-    for (int j = 0; j < NB / 16; ++j) {
+    for (int j = 0; j < NB / 32; ++j) {
         const int i = t + kThreads * j;
         uint4 h, l;
         split_tf32(x.b[j][0], h.x, l.x); split_tf32(x.b[j][1], h.y, l.y);
@@ -253,7 +256,7 @@ __device__ __forceinline__ void store_chunk(const Chunk<NB>& x, unsigned char* s
 // MODE 0: gram, blockIdx.x = M tile, blockIdx.y = K split.
 // MODE 1: update, blockIdx.x = M tile (rows), one CTA covers all of K.
 template <int MODE, int NB>
-__global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramArgs g) {
+__global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramArgs g) {
     using S = TcSmem<NB>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -337,11 +340,14 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramArgs g) {
     if (!all_ok) {
         if (t == 0) atomicExch(g.flag, 1);
     } else if (c_end > c_begin) {
-        // epilogue: thread t holds accumulator row t (lane t), columns 0..NB-1
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        float acc[NB];
+        // epilogue: accumulator row t % 128 (lane t % 128; warp w reads lanes
+        // 32 (w % 4) ..), columns NB/2 (t / 128) .. NB/2 (t / 128) + NB/2 - 1
+        constexpr int NH = NB / 2;
+        const int half = t / kM;
+        const uint32_t taddr = tmem + ((uint32_t)((warp % 4) * 32) << 16) + (uint32_t)(half * NH);
+        float acc[NH];
 #pragma unroll
-        for (int j0 = 0; j0 < NB; j0 += 16) {
+        for (int j0 = 0; j0 < NH; j0 += 16) {
             uint32_t r[16];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
@@ -354,15 +360,16 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramArgs g) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) acc[j0 + e] = __uint_as_float(r[e]);
         }
-        const int64_t m = m0 + t;
+        const int64_t m = m0 + t % kM;
         if (m < g.M) {
 #pragma unroll
-            for (int n = 0; n < NB; ++n) {
+            for (int j = 0; j < NH; ++j) {
+                const int n = half * NH + j;
                 if (n >= g.N) break;
                 if (MODE == 0) {
-                    atomicAdd(g.C + m + (int64_t)n * g.ldc, (double)acc[n]);
+                    atomicAdd(g.C + m + (int64_t)n * g.ldc, (double)acc[j]);
                 } else {
-                    g.C[m + (int64_t)n * g.ldc] = g.F[m + (int64_t)n * g.ldf] - (double)acc[n];
+                    g.C[m + (int64_t)n * g.ldc] = g.F[m + (int64_t)n * g.ldf] - (double)acc[j];
                 }
             }
         }
