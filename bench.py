@@ -244,7 +244,8 @@ def workload_for(cfg: str, slices: int = 0) -> W.Workload:
     elif cfg in ("2", "3", "5"):
         w = W.CONFIGS[cfg]()
     else:
-        raise SystemExit("--config must be 2, 3, 5 or 4:<instance> for a sweep, 4 for the batch or snapshot")
+        raise SystemExit("--config must be 2, 3, 5 or 4:<instance> for a sweep, 4 for the batch, snapshot or "
+                         "parareal")
     if slices and slices != w.n_slices:
         m_f = w.m_f
         w.t_final = w.t_final * slices / w.n_slices
@@ -667,6 +668,22 @@ def run_ours(a) -> int:
     return 0
 
 
+# ---------------------------------------------------------------- the parareal line alone
+def run_parareal(a) -> int:
+    """Alg. 3 with the Procrustes corrector on the 512^2 x 32 workload to a
+    1e-4 relative energy-norm error, as in the sweep line's `parareal` object,
+    printed on its own (one JSON line; a short command for profiling the
+    correction path)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    r = parareal_time_to_tol(dev)
+    out = {"metric": "parareal_time_to_1e-4", "impl": "ours", "unit": "ms", "value": r["parareal_ms"],
+           "higher_is_better": False, "data": "synthetic", "config": {"workload": r["workload"]}, "parareal": r}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- snapshot products (Alg. 1)
 def run_snapshot(a) -> int:
     """The two tall products of UpdateSVD on the tensor cores (split-TF32,
@@ -725,7 +742,7 @@ def main(argv=None) -> int:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="3",
                     help="2, 3, 5: the sweep workloads; 4: the uneven batch; 4:<i>: instance i of the batch "
-                         "alone; snapshot: the tensor-core products of UpdateSVD")
+                         "alone; snapshot: the tensor-core products of UpdateSVD; parareal: the parareal line")
     ap.add_argument("--block-depth", type=int, default=0, help="0 = library default")
     ap.add_argument("--columns", type=int, default=0, choices=[0, 2, 4],
                     help="fused-kernel columns per thread (0 = library default)")
@@ -749,6 +766,8 @@ def main(argv=None) -> int:
         return run_batch(a)
     if a.config == "snapshot":
         return run_snapshot(a)
+    if a.config == "parareal":
+        return run_parareal(a)
     return run_ours(a)
 
 

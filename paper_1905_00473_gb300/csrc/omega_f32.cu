@@ -2,7 +2,9 @@
 // serial update; X = Xb WX, Y = Yb WY from Alg. 1), for FP32 contexts: the
 // two tall products read single-precision copies of the stored bases Xb, Yb
 // (half the bytes of the FP64 arrays; these matrix-vector products are bound
-// by HBM), multiply in FP32 and accumulate every eight products into FP64.
+// by HBM), multiply in FP32 and add every eight products into a compensated
+// (Kahan) FP32 sum, which reaches FP64 only per thread and in the block
+// reductions (FP64 adds per product group held the FP64 pipe at 68 %).
 // Each result is FP32-accurate, as the context's state is; a zero d still
 // gives exactly zero, so the serial sweep's finite termination (Sec. 3.3)
 // is unaffected.  The small products with WX, WY stay FP64.
@@ -20,6 +22,15 @@
 namespace {
 
 constexpr int kOmT = 256;
+
+// s + y in compensated FP32 (Kahan): c carries the low-order bits lost so far
+__device__ __forceinline__ void kahan_add(float& s, float& c, float y) {
+    const float yy = __fsub_rn(y, c);
+    const float t = __fadd_rn(s, yy);
+    c = __fsub_rn(__fsub_rn(t, s), yy);
+    s = t;
+}
+__device__ __forceinline__ double kahan_value(float s, float c) { return (double)s - (double)c; }
 
 __global__ void om_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t m) {
     for (int64_t i = (int64_t)blockIdx.x * kOmT + threadIdx.x; i < m; i += (int64_t)gridDim.x * kOmT)
@@ -42,9 +53,9 @@ __global__ void __launch_bounds__(kOmT) om_gemv_t(const float* __restrict__ Ys, 
     const int64_t q4 = rows / 4;
     const int64_t per = (q4 + kOmR - 1) / kOmR;
     const int64_t qa = blockIdx.y * per, qb = min(q4, qa + per);
-    double sa = 0.0, sb = 0.0;
+    float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
     int64_t i = qa + threadIdx.x;
-    for (; i + kOmT < qb; i += 2 * kOmT) {   // eight FP32 products, then one FP64 add
+    for (; i + kOmT < qb; i += 2 * kOmT) {   // eight FP32 products, then one compensated add
         const float4 g0 = __ldg(g4 + i), g1 = __ldg(g4 + i + kOmT);
         const float4 x0 = __ldcs(a4 + i), x1 = __ldcs(a4 + i + kOmT);
         const float4 y0 = __ldcs(b4 + i), y1 = __ldcs(b4 + i + kOmT);
@@ -56,8 +67,8 @@ __global__ void __launch_bounds__(kOmT) om_gemv_t(const float* __restrict__ Ys, 
         fa = fmaf(x1.y, g1.y, fa); fb = fmaf(y1.y, g1.y, fb);
         fa = fmaf(x1.z, g1.z, fa); fb = fmaf(y1.z, g1.z, fb);
         fa = fmaf(x1.w, g1.w, fa); fb = fmaf(y1.w, g1.w, fb);
-        sa += (double)fa;
-        sb += (double)fb;
+        kahan_add(sa, ca, fa);
+        kahan_add(sb, cb, fb);
     }
     for (; i < qb; i += kOmT) {
         const float4 g0 = __ldg(g4 + i), x0 = __ldcs(a4 + i), y0 = __ldcs(b4 + i);
@@ -65,11 +76,11 @@ __global__ void __launch_bounds__(kOmT) om_gemv_t(const float* __restrict__ Ys, 
         fa = fmaf(x0.y, g0.y, fa); fb = fmaf(y0.y, g0.y, fb);
         fa = fmaf(x0.z, g0.z, fa); fb = fmaf(y0.z, g0.z, fb);
         fa = fmaf(x0.w, g0.w, fa); fb = fmaf(y0.w, g0.w, fb);
-        sa += (double)fa;
-        sb += (double)fb;
+        kahan_add(sa, ca, fa);
+        kahan_add(sb, cb, fb);
     }
-    red[0][threadIdx.x] = sa;
-    red[1][threadIdx.x] = sb;
+    red[0][threadIdx.x] = kahan_value(sa, ca);
+    red[1][threadIdx.x] = kahan_value(sb, cb);
     __syncthreads();
     for (int s = kOmT / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
@@ -105,9 +116,9 @@ __global__ void __launch_bounds__(kOmT) om_gemv_n(const float* __restrict__ Xs, 
     __syncthreads();
     const int64_t i4 = (int64_t)blockIdx.x * kOmT + threadIdx.x;
     if (4 * i4 >= rows) return;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
     int j = ja;
-    for (; j + 8 <= jb; j += 8) {   // eight FP32 products per row, then one FP64 add
+    for (; j + 8 <= jb; j += 8) {   // eight FP32 products per row, then one compensated add
         float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -118,15 +129,22 @@ __global__ void __launch_bounds__(kOmT) om_gemv_n(const float* __restrict__ Xs, 
             f2 = fmaf(x.z, t, f2);
             f3 = fmaf(x.w, t, f3);
         }
-        s0 += (double)f0; s1 += (double)f1; s2 += (double)f2; s3 += (double)f3;
+        kahan_add(s[0], cmp[0], f0);
+        kahan_add(s[1], cmp[1], f1);
+        kahan_add(s[2], cmp[2], f2);
+        kahan_add(s[3], cmp[3], f3);
     }
     for (; j < jb; ++j) {
         const float4 x = __ldcs((const float4*)(Xs + (int64_t)j * rows) + i4);
         const float t = ts[j - ja];
-        s0 += (double)(x.x * t); s1 += (double)(x.y * t); s2 += (double)(x.z * t); s3 += (double)(x.w * t);
+        kahan_add(s[0], cmp[0], x.x * t);
+        kahan_add(s[1], cmp[1], x.y * t);
+        kahan_add(s[2], cmp[2], x.z * t);
+        kahan_add(s[3], cmp[3], x.w * t);
     }
     double* o = part + (int64_t)c * rows + 4 * i4;
-    o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) o[e] = kahan_value(s[e], cmp[e]);
 }
 
 // out[i] = sum_c part[c][i], chunks in order

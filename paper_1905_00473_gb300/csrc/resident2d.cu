@@ -28,6 +28,7 @@ namespace {
 constexpr int kRsCl = 8;     // CTAs per cluster (one slice per cluster)
 constexpr int kRsT = 512;    // threads per CTA (one 4-point quad each at n = 128)
 constexpr int kRsMaxPasses = 64;
+constexpr int kRsQ = 4;      // 4-point quads per thread at most (n = 256: 32 rows x 64 quads / 512)
 
 struct ResParams {
     const float* u_in;
@@ -52,7 +53,11 @@ __device__ __forceinline__ float rs_bf16_round(float r) {
     return __uint_as_float(w << 16);
 }
 
-__global__ void __cluster_dims__(kRsCl, 1, 1) __launch_bounds__(kRsT) resident2d_kernel(ResParams p) {
+// Q: 4-point quads per thread (1 at n = 128, up to kRsQ at n = 256); with one
+// quad the kernel fits 64 registers, so two CTAs share an SM
+template <int Q>
+__global__ void __cluster_dims__(kRsCl, 1, 1) __launch_bounds__(kRsT, Q == 1 ? 2 : 1)
+    resident2d_kernel(ResParams p) {
     extern __shared__ float rs_sm[];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -80,6 +85,19 @@ __global__ void __cluster_dims__(kRsCl, 1, 1) __launch_bounds__(kRsT) resident2d
     const float* const du_s1 = cl.map_shared_rank(dub[1], rs);
     const float* const du_n0 = cl.map_shared_rank(dub[0], rn);
     const float* const du_n1 = cl.map_shared_rank(dub[1], rn);
+    // this thread's quads (the same at every level): row, first column and
+    // the periodic left / right neighbour columns, computed once
+    int qr[Q], qc[Q], ql[Q], qx[Q];
+    const int nquads = hn / 4;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const int q = threadIdx.x + k * kRsT;
+        const int r = q / nq, c0 = 4 * (q - r * nq);
+        qr[k] = r;
+        qc[k] = c0;
+        ql[k] = c0 == 0 ? n - 1 : c0 - 1;
+        qx[k] = c0 + 4 == n ? 0 : c0 + 4;
+    }
     cl.sync();
     const float dt = p.dt;
     int cur = 0;
@@ -88,15 +106,17 @@ __global__ void __cluster_dims__(kRsCl, 1, 1) __launch_bounds__(kRsT) resident2d
         const int g0 = ps * p.depth;
         const int levels = last ? p.last_levels : p.depth;
         // D0 = ((W - C) + (E - C)) + ((S - C) + (N - C)) of u_hi
-        for (int q = threadIdx.x; q < hn / 4; q += kRsT) {
-            const int r = q / nq, c0 = 4 * (q - r * nq);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            if (threadIdx.x + j * kRsT >= nquads) break;
+            const int r = qr[j], c0 = qc[j];
             const float* rowc = uh + r * n;
             const float* rows = r > 0 ? uh + (r - 1) * n : uh_s + (H - 1) * n;
             const float* rown = r < H - 1 ? uh + (r + 1) * n : uh_n;
             const float4 C = *(const float4*)(rowc + c0);
             const float4 S = *(const float4*)(rows + c0);
             const float4 N = *(const float4*)(rown + c0);
-            const float xl = rowc[(c0 + n - 1) % n], xr = rowc[(c0 + 4) % n];
+            const float xl = rowc[ql[j]], xr = rowc[qx[j]];
             const float cc[4] = {C.x, C.y, C.z, C.w}, ss[4] = {S.x, S.y, S.z, S.w}, nn[4] = {N.x, N.y, N.z, N.w};
             float o[4];
 #pragma unroll
@@ -115,8 +135,10 @@ __global__ void __cluster_dims__(kRsCl, 1, 1) __launch_bounds__(kRsT) resident2d
             float* dn = cur ? dub[0] : dub[1];
             const float* du_s = cur ? du_s1 : du_s0;
             const float* du_n = cur ? du_n1 : du_n0;
-            for (int q = threadIdx.x; q < hn / 4; q += kRsT) {
-                const int r = q / nq, c0 = 4 * (q - r * nq);
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                if (threadIdx.x + j * kRsT >= nquads) break;
+                const int r = qr[j], c0 = qc[j];
                 const float* rowc = du + r * n;
                 const float* rows = r > 0 ? du + (r - 1) * n : du_s + (H - 1) * n;
                 const float* rown = r < H - 1 ? du + (r + 1) * n : du_n;
@@ -126,7 +148,7 @@ __global__ void __cluster_dims__(kRsCl, 1, 1) __launch_bounds__(kRsT) resident2d
                 const float4 D = *(const float4*)(d0 + r * n + c0);
                 const float4 K = *(const float4*)(kp + r * n + c0);
                 const float4 V = *(const float4*)(vv + r * n + c0);
-                const float xl = rowc[(c0 + n - 1) % n], xr = rowc[(c0 + 4) % n];
+                const float xl = rowc[ql[j]], xr = rowc[qx[j]];
                 const float cc[4] = {C.x, C.y, C.z, C.w}, ss[4] = {S.x, S.y, S.z, S.w};
                 const float nn[4] = {N.x, N.y, N.z, N.w}, dd[4] = {D.x, D.y, D.z, D.w};
                 const float kk[4] = {K.x, K.y, K.z, K.w}, vi[4] = {V.x, V.y, V.z, V.w};
@@ -189,7 +211,7 @@ bool pr_resident2d_supported(const pr_ctx* ctx) {
     const int64_t n = ctx->n;
     if (n % (4 * kRsCl) != 0) return false;
     const int64_t H = n / kRsCl;
-    if (6 * H * n * 4 > 227 * 1024) return false;
+    if (6 * H * n * 4 > 227 * 1024 || H * (n / 4) > (int64_t)kRsQ * kRsT) return false;
     int passes = 0, last_levels = 0;
     rs_plan(ctx, passes, last_levels);
     // the per-pass plan runs lone levels through the one-level kernel (another
@@ -212,9 +234,11 @@ pr_status pr_launch_resident2d(pr_ctx* ctx, const void* u_in, const void* v_in, 
     rs_plan(ctx, p.passes, p.last_levels);
     p.dt = (float)ctx->dt_f;
     const size_t smem = (size_t)6 * (ctx->n / kRsCl) * ctx->n * 4;
-    cudaError_t e = cudaFuncSetAttribute(resident2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t quads = (ctx->n / kRsCl) * (ctx->n / 4);
+    auto kern = quads <= kRsT ? resident2d_kernel<1> : resident2d_kernel<kRsQ>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "resident2d: shared memory attribute");
-    resident2d_kernel<<<nslices * kRsCl, kRsT, smem, st>>>(p);
+    kern<<<nslices * kRsCl, kRsT, smem, st>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "resident2d launch");
     return PR_OK;
