@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(kOmT) om_gemv_t(const float* __restrict__ Ys, 
     const int64_t qa = blockIdx.y * per, qb = min(q4, qa + per);
     float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
     int64_t i = qa + threadIdx.x;
+#pragma unroll 2
     for (; i + kOmT < qb; i += 2 * kOmT) {   // eight FP32 products, then one compensated add
         const float4 g0 = __ldg(g4 + i), g1 = __ldg(g4 + i + kOmT);
         const float4 x0 = __ldcs(a4 + i), x1 = __ldcs(a4 + i + kOmT);

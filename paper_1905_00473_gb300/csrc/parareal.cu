@@ -928,8 +928,8 @@ constexpr double kEigFloor = 1e-6;
 // SVD of H (h x h) for FP32 contexts from the symmetric eigenproblem of
 // H^T H (cuSOLVER syevd, several times faster than gesvd at h ~ 500):
 // H^T H = V Lambda V^T gives Y_h = V (descending order) and sigma =
-// sqrt(lambda); X_h is the orthonormal polar factor of H V Sigma^-1 (two
-// Newton-Schulz steps), which restores the orthogonality that the squared
+// sqrt(lambda); X_h is the orthonormal polar factor of H V Sigma^-1 (one or
+// two Newton-Schulz steps), which restores the orthogonality that the squared
 // spectrum loses for the small sigma.  Fills
 // d->Xh, d->YhT (rows 0..r-1), d->sig and `sig`; *used = false (nothing
 // written) when a kept sigma lies below kEigFloor sigma_max.
@@ -937,7 +937,8 @@ pr_status svd_eig_(pr_ctx* ctx, pr_driver* d, int h, double tol, std::vector<dou
                    cudaStream_t st) {
     const double one = 1.0, zero = 0.0;
     used = false;
-    PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, h, h, h, &one, d->H, h, d->H, h, &zero, d->E, h), "H^T H");
+    // H^T H, lower triangle only (what syevd reads): half the FP64 flops of a GEMM
+    PR_BLAS(ctx, cublasDsyrk(d->blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, h, h, &one, d->H, h, &zero, d->E, h), "H^T H");
     int lw = 0;
     PR_BLAS(ctx, cusolverDnDsyevd_bufferSize(d->sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, h, d->E, h,
                                              d->sig, &lw), "syevd size");
@@ -962,25 +963,33 @@ pr_status svd_eig_(pr_ctx* ctx, pr_driver* d, int h, double tol, std::vector<dou
     PR_BLAS(ctx, cublasDgeam(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, r, h, &one, d->Xh, h, &zero, d->Xh, r, d->YhT, h),
             "V^T");
     // X_h = the orthonormal polar factor of U0 = H V Sigma^-1.  The
-    // eigenproblem leaves U0 within ~u (sigma_1 / sigma_r)^2 <= 1e-4 of
+    // eigenproblem leaves U0 within delta ~ u (sigma_1 / sigma_r)^2 <= 1e-4 of
     // orthonormal (sigma_r >= kEigFloor sigma_1); each Newton-Schulz step
-    // X <- X (3 I - X^T X) / 2 squares that distance, so two reach FP64
-    // accuracy (four FP64 GEMMs, in place of a latency-bound Householder QR)
+    // X <- X (3 I - X^T X) / 2 takes delta to ~1.5 delta^2 (in place of a
+    // latency-bound Householder QR).  One step when delta <= 1e-5 (FP32
+    // contexts: ~1e-10 after it; every kept ratio sigma_r / sigma_1 above
+    // ~5e-6, so the default rank cut of 1e-5), else two.  The Gram matrix
+    // is a symmetric rank-k product and the update a symmetric multiply.
     PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, h, r, h, &one, d->H, h, d->Xh, h, &zero, d->E, h), "H V");
     std::vector<double> inv(r);
     for (int i = 0; i < r; ++i) inv[i] = 1.0 / sig[i];
     cudaMemcpyAsync(d->rsign, inv.data(), (size_t)r * 8, cudaMemcpyHostToDevice, st);
     scale_cols<<<blocks_for((int64_t)h * r), kT, 0, st>>>(d->E, d->rsign, d->Xh, h, r);
+    const double kappa = sig[0] / sig[r - 1];
+    const int ns_steps = 2.2e-16 * kappa * kappa <= 1e-5 ? 1 : 2;
     double* nsb[2] = {d->Xh, d->H};   // H is not needed past this point
-    for (int step = 0; step < 2; ++step) {
+    for (int step = 0; step < ns_steps; ++step) {
         double* X = nsb[step & 1];
         double* Xn = nsb[(step + 1) & 1];
-        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_T, CUBLAS_OP_N, r, r, h, &one, X, h, X, h, &zero, d->E, r),
+        PR_BLAS(ctx, cublasDsyrk(d->blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, r, h, &one, X, h, &zero, d->E, r),
                 "X^T X");
-        ns_coef<<<blocks_for((int64_t)r * r), kT, 0, st>>>(d->E, r);
-        PR_BLAS(ctx, cublasDgemm(d->blas, CUBLAS_OP_N, CUBLAS_OP_N, h, r, r, &one, X, h, d->E, r, &zero, Xn, h),
+        ns_coef<<<blocks_for((int64_t)r * r), kT, 0, st>>>(d->E, r);   // the upper triangle is not read
+        PR_BLAS(ctx, cublasDsymm(d->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, h, r, &one, d->E, r, X, h, &zero,
+                                 Xn, h),
                 "X (3I - X^T X)/2");
     }
+    if (ns_steps == 1)   // the result is in H's storage
+        cudaMemcpyAsync(d->Xh, d->H, (size_t)h * r * 8, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(d->sig, sig.data(), (size_t)h * 8, cudaMemcpyHostToDevice, st);
     e = cudaStreamSynchronize(st);   // `sig` is a host vector the copy reads
     if (e != cudaSuccess) return pr_cuda_fail(ctx, e, "svd_eig");

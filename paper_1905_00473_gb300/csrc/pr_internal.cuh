@@ -100,7 +100,7 @@ pr_status cholqr2_launch(double* A, int64_t rows, int nc, double* R, double* ws,
 
 // ---- the Procrustes corrector applied with FP32 copies of the bases (omega_f32.cu)
 // Stored columns hb <= kOmMaxCols, rows % 4 == 0 (PR_EINVAL otherwise).
-constexpr int kOmJ = 8;              // column chunks of the out = Xs t2 product
+constexpr int kOmJ = 16;             // column chunks of the out = Xs t2 product
 constexpr int kOmR = 4;              // row parts of the t1 = Ys^T g product
 constexpr int kOmMaxCols = 8192;
 pr_status omega_f32_supported(int64_t rows, int hb);
