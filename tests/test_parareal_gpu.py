@@ -307,3 +307,45 @@ def test_update_svd_fp32_context_matches_oracle(lib):
         ref = U @ (V.T @ g)
         assert np.linalg.norm(out.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref), k
     binding.pr_check(ctx)
+
+
+@pytest.mark.parametrize("case", ["dependent", "in_span"])
+def test_fp32_update_svd_with_degenerate_blocks(lib, case):
+    """UpdateSVD in an FP32 context (tensor-core products, Cholesky QR twice,
+    eigenproblem SVD with the Newton-Schulz re-orthonormalisation, the FP32
+    copies of the bases in the apply) on blocks the QR must handle: columns
+    that repeat earlier ones ("dependent") and a second block that lies in the
+    span of the first ("in_span", the deflated residual is rounding noise).
+    Omega g matches the oracle's X Y^T g to FP32 accuracy and the rank agrees."""
+    import torch
+    from paper_1905_00473_gb300 import binding
+    w = _case(2, 64, 8, 8, "f32", 4)
+    ctx = _ctx(w, 4, tol=1e-5)
+    rows = ctx.rows
+    rng = np.random.default_rng(11)
+    base_f = rng.standard_normal((rows, 8)) * np.logspace(0, -1.5, 8)
+    base_g = rng.standard_normal((rows, 8)) * np.logspace(0, -1.5, 8)
+    blocks = []
+    if case == "dependent":
+        F, G = base_f.copy(), base_g.copy()
+        F[:, 5] = F[:, 1]
+        F[:, 7] = 2.0 * F[:, 0] - F[:, 2]
+        G[:, 6] = G[:, 3]
+        blocks.append((F, G))
+    else:
+        blocks.append((base_f, base_g))
+        mix = rng.standard_normal((8, 8))
+        blocks.append((base_f @ mix, base_g @ mix))
+    U = S = V = None
+    for F, G in blocks:
+        binding.pr_procrustes_correct(ctx, torch.tensor(F.T.copy(), device="cuda"),
+                                      torch.tensor(G.T.copy(), device="cuda"))
+        U, S, V = procrustes.update_svd(U, S, V, F, G, 1e-5)
+        g = rng.standard_normal(rows)
+        out = torch.zeros(rows, dtype=torch.float64, device="cuda")
+        rk = binding.pr_procrustes_apply(ctx, torch.tensor(g, device="cuda"), out)
+        binding.pr_check(ctx)
+        assert rk == S.size, (rk, S.size)
+        ref = U @ (V.T @ g)
+        err = np.linalg.norm(out.cpu().numpy() - ref) / np.linalg.norm(g)
+        assert err <= 1e-5, err
