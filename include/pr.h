@@ -245,14 +245,21 @@ pr_status pr_iterate_corrector_phases(const pr_ctx* ctx, double* ms, int* eig_sv
  *                block first), 1 <= ncols <= N.
  * X and Y are held factored (X = X_b W_X): every update appends its ncols
  * orthonormalised columns to X_b, Y_b in context memory (2 (d+1) n_c^d
- * doubles per column) until pr_procrustes_reset or the next pr_iterate.
+ * doubles per column, plus single-precision copies in FP32 contexts) until
+ * pr_procrustes_reset or the next pr_iterate.  FP32 contexts form the tall
+ * products on the tensor cores (below), the QR of the deflated blocks by
+ * Cholesky QR twice (columns dependent on earlier ones to working accuracy
+ * get a zero column of Q) and the SVD from the eigenproblem of H^T H; FP64
+ * contexts use FP64 BLAS, Householder QR and gesvd throughout.
  * Synchronises the stream. */
 pr_status pr_procrustes_correct(pr_ctx* ctx, const double* Fcols, const double* Gcols, int ncols,
                                 void* stream);
 
 /* pr_procrustes_apply -- out = X Y^T g (the phase corrector Omega of Alg. 3)
  * for a DEVICE double vector g of (d+1) n_c^d entries; *rank (host, may be
- * NULL) receives s.  g == NULL only reports the rank. */
+ * NULL) receives s.  g == NULL only reports the rank.  FP32 contexts read
+ * single-precision copies of the stored bases (FP32 products, compensated
+ * sums; FP32-accurate, and exactly zero for g = 0); FP64 contexts are FP64. */
 pr_status pr_procrustes_apply(pr_ctx* ctx, const double* g, double* out, int* rank, void* stream);
 
 /* pr_procrustes_reset -- forget M (S empty, as at the start of Alg. 3). */
