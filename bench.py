@@ -540,6 +540,8 @@ def run_ours(a) -> int:
                             block_depth=a.block_depth)
     if a.columns:
         binding.pr_set_fused_columns(ctx, a.columns)
+    if a.wide_rows:
+        binding.pr_set_wide_rows(ctx, a.wide_rows)
     binding.pr_set_one_launch(ctx, a.one_launch == "on")
     info = binding.pr_info(ctx)
     u_in = u_pin.to(dev)
@@ -752,6 +754,8 @@ def main(argv=None) -> int:
     ap.add_argument("--instances", type=int, default=48, help="--config 4: instances in the batch (all 48)")
     ap.add_argument("--no-parareal", action="store_true",
                     help="skip the parareal time-to-1e-4 measurement")
+    ap.add_argument("--wide-rows", type=int, default=0, choices=[0, 1, 2],
+                    help="2048-point rows at depth 8: 1 cluster rows, 2 x-strips (0 = library default)")
     ap.add_argument("--one-launch", choices=["on", "off"], default="off",
                     help="on: a whole sweep in one persistent launch where supported; off (library default): "
                          "one launch per pass")

@@ -390,6 +390,17 @@ pr_status pr_set_fused_columns(pr_ctx* ctx, int columns);
  * next call. */
 pr_status pr_set_one_launch(pr_ctx* ctx, int on);
 
+/* pr_set_wide_rows -- how the fused 2D FP32 passes at depth 8 hold the
+ * 2048-point rows, which no single CTA's registers hold: 1 = each row shared
+ * by a two-CTA thread-block cluster that exchanges the half-rows' x-edges
+ * through distributed shared memory; 2 = three overlapping x-strips of 704
+ * columns per row (688 final columns, an 8-column halo each side recomputed
+ * by the neighbouring strip), no exchange; the default, measured 6 % faster
+ * on a GB300.  Both compute the same level recurrence in the same order
+ * (bit-identical results).  PR_EINVAL for another mode.  Takes effect at the
+ * next call. */
+pr_status pr_set_wide_rows(pr_ctx* ctx, int mode);
+
 /* pr_set_resident -- where a 2D FP32 slice fits in the shared memory of one
  * thread-block cluster (n = 128 or 256 at block depth 8 with four columns
  * per thread), on != 0 makes pr_fine_all_slices propagate every slice in ONE

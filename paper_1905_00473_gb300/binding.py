@@ -79,6 +79,7 @@ _SIGNATURES = {
     "pr_debug_stall_waits": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_set_one_launch": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_set_resident": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pr_set_wide_rows": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_serial_sweep": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "pr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -501,6 +502,11 @@ def pr_iterate_adjoint(ctx: Context, u0, p0, K: int, corrector: int, gu_T, gv_T,
 def pr_set_one_launch(ctx: Context, on: bool) -> None:
     """Whole sweep in one persistent launch, or one launch per pass (the default)."""
     _check(load().pr_set_one_launch(ctx.handle, 1 if on else 0), ctx.handle)
+
+
+def pr_set_wide_rows(ctx: Context, mode: int) -> None:
+    """2048-point rows at depth 8: 1 = two-CTA cluster rows, 2 = x-strips."""
+    _check(load().pr_set_wide_rows(ctx.handle, int(mode)), ctx.handle)
 
 
 def pr_set_resident(ctx: Context, on: bool) -> None:

@@ -511,6 +511,13 @@ extern "C" pr_status pr_set_fused_columns(pr_ctx* ctx, int columns) {
     return PR_OK;
 }
 
+extern "C" pr_status pr_set_wide_rows(pr_ctx* ctx, int mode) {
+    if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_set_wide_rows: ctx is NULL");
+    if (mode != 1 && mode != 2) return pr_fail(ctx, PR_EINVAL, "pr_set_wide_rows: mode must be 1 or 2");
+    ctx->wide_rows = mode;
+    return PR_OK;
+}
+
 extern "C" pr_status pr_set_resident(pr_ctx* ctx, int on) {
     if (!ctx) return pr_fail(nullptr, PR_EINVAL, "pr_set_resident: ctx is NULL");
     ctx->resident = on != 0;

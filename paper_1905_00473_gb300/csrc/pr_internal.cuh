@@ -48,6 +48,7 @@ struct pr_ctx {
     pr_alloc_fn ualloc = nullptr;     // the caller allocator at creation (pr_set_allocator), or cudaMalloc
     pr_release_fn urelease = nullptr;
     void* uarg = nullptr;
+    int wide_rows = 2;              // n = 2048 at depth 8: 1 cluster rows, 2 x-strips (pr_set_wide_rows)
     int resident = -1;              // slices held in one cluster's shared memory: -1 auto (n <= 128), 0 off, 1 on
     std::string err;
     // pr_profile: event pairs around launches, by kernel kind

@@ -263,9 +263,11 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
 
     // ---- the finished row's u_hi, fetched early from L2 ------------------
     const int rho_out = i - B;
-    // in an x-strip only the columns at least XH from both strip edges are final
+    // in an x-strip only the columns at least XH from both strip edges are
+    // final, and of the last strip of a row only those below n (strips of a
+    // width that does not divide n overlap the first strip there)
     const bool do_out = rho_out >= L && rho_out < L + sg.H &&
-                        (XH == 0 || (t >= XH / kCpt && t < NT - XH / kCpt));
+                        (XH == 0 || (t >= XH / kCpt && t < NT - XH / kCpt && sg.x0 + kCpt * t < n));
     int64_t off_out = 0;
     float4 u0o = make_float4(0.f, 0.f, 0.f, 0.f);
     if (do_out) {
@@ -584,7 +586,7 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
 // XH = 0: a CTA holds whole periodic rows (n = 4 NT).  XH > 0: it holds
 // x-strips of 4 NT columns, of which the middle 4 NT - 2 XH are final (the
 // stencil's reach grows one column per level, so XH >= B), and the rows of a
-// slice are covered by n / (4 NT - 2 XH) strips.
+// slice are covered by ceil(n / (4 NT - 2 XH)) strips.
 // The ring mbarriers (and, for cluster rows, the exchange mbarriers), armed
 // once per launch by thread 0.
 template <int NT, int B, int CL>
@@ -644,7 +646,7 @@ __device__ __forceinline__ bool tb2d_pass(const Tb2dParams& p, unsigned char* sm
 
     // rows_total counts n rows per (slice, strip) pair
     constexpr int kStripW = S::W - 2 * XH;
-    const int strips = XH ? n / kStripW : 1;
+    const int strips = XH ? (n + kStripW - 1) / kStripW : 1;
     for (int64_t seg0 = r_begin; seg0 < r_end && !aborted;) {
         Seg sg;
         const int64_t vslice = seg0 / n;
@@ -798,7 +800,7 @@ pr_status launch_cfg(pr_ctx* ctx, const pr_pass& ps, cudaStream_t st) {
     p.v_out = (float*)ps.v_out;
     p.r_out = (uint16_t*)ps.r_out;
     p.flag = ctx->dev_flag;
-    const int strips = XH ? (int)ctx->n / (Smem<NT, B>::W - 2 * XH) : 1;
+    const int strips = XH ? ((int)ctx->n + Smem<NT, B>::W - 2 * XH - 1) / (Smem<NT, B>::W - 2 * XH) : 1;
     p.rows_total = (int64_t)ps.nslices * strips * ctx->n;
     p.n = (int)ctx->n;
     p.g0 = ps.g0;

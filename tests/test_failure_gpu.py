@@ -10,17 +10,19 @@ from tests import _parity as P
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,m_f", [(256, 7), (2048, 7), (256, 23)])
-def test_bounded_wait_times_out_and_context_recovers(lib, n, m_f):
-    """m_f = 7: one fused pass of 8 levels (whole rows per CTA; rows shared by
-    a 2-CTA cluster at n = 2048); m_f = 23: three passes in one persistent
-    launch, whose grid barrier every CTA still reaches after giving up."""
+@pytest.mark.parametrize("n,m_f,wide", [(256, 7, 2), (2048, 7, 1), (2048, 7, 2), (256, 23, 2)])
+def test_bounded_wait_times_out_and_context_recovers(lib, n, m_f, wide):
+    """m_f = 7: one fused pass of 8 levels (whole rows per CTA; at n = 2048
+    rows shared by a 2-CTA cluster, wide = 1, or x-strips, wide = 2); m_f =
+    23: three passes in one persistent launch, whose grid barrier every CTA
+    still reaches after giving up."""
     import time
     import torch
     from paper_1905_00473_gb300 import binding
     w = W.custom_case(2, n, 2, m_f, "f32", "smooth")
     ctx = P.make_ctx(w)
     assert binding.pr_info(ctx)["block_depth"] == 8
+    binding.pr_set_wide_rows(ctx, wide)
     binding.pr_set_one_launch(ctx, m_f == 23)
     u, v = W.slice_states(w, seed=1)
     ud = torch.tensor(u, dtype=torch.float32, device="cuda")

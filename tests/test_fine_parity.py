@@ -73,14 +73,15 @@ def test_fused_2d_strips_2048(lib, m_f, N):
     (7, 1, (1, 0)),    # 8 levels in one general pass (half kicks at both ends)
 ])
 def test_fused_2d_cluster_rows_2048(lib, m_f, N, passes):
-    """n = 2048 at depth 8 (the default) shares every row between the two CTAs
-    of a thread-block cluster, which exchange the x-edges of their half-rows
-    through distributed shared memory.  The periodic wrap in x crosses from
-    one CTA to the other at both ends; rows of several slices are split
-    across the clusters."""
+    """n = 2048 at depth 8 with the cluster rows (pr_set_wide_rows 1): every
+    row shared by the two CTAs of a thread-block cluster, which exchange the
+    x-edges of their half-rows through distributed shared memory.  The
+    periodic wrap in x crosses from one CTA to the other at both ends; rows
+    of several slices are split across the clusters."""
     from paper_1905_00473_gb300 import binding
     w = W.custom_case(2, 2048, N, m_f, "f32", "inclusion", seed=20 + m_f)
     ctx = P.make_ctx(w)
+    binding.pr_set_wide_rows(ctx, 1)
     assert binding.pr_info(ctx)["block_depth"] == 8
     u, v = W.slice_states(w, seed=12)
     binding.pr_profile(ctx, True)
@@ -89,16 +90,18 @@ def test_fused_2d_cluster_rows_2048(lib, m_f, N, passes):
     assert (binding.pr_profile_read(ctx, 0)[0], binding.pr_profile_read(ctx, 1)[0]) == passes
 
 
-def test_fused_2d_cluster_rows_2048_whole_slices(lib):
-    """160 slices of 2048^2: a cluster's row range holds whole slices, whose
-    halo rows wrap around the periodic slice at both ends.  Four distinct
-    slice states are tiled over the batch; the first, two middle and the last
-    slices are checked against the oracle."""
+@pytest.mark.parametrize("wide", [1, 2])
+def test_fused_2d_cluster_rows_2048_whole_slices(lib, wide):
+    """160 slices of 2048^2, in cluster rows (1) or x-strips (2): a row range
+    holds whole slices, whose halo rows wrap around the periodic slice at
+    both ends.  Four distinct slice states are tiled over the batch; the
+    first, two middle and the last slices are checked against the oracle."""
     import torch
     from paper_1905_00473_gb300 import binding
     N = 160
     w = W.custom_case(2, 2048, N, 9, "f32", "inclusion")   # 10 levels: 8 + 2
     ctx = P.make_ctx(w)
+    binding.pr_set_wide_rows(ctx, wide)
     w4 = W.custom_case(2, 2048, 4, 9, "f32", "inclusion")
     u4, v4 = W.slice_states(w4, seed=13)
     u4d = torch.tensor(u4, dtype=torch.float32, device="cuda")
@@ -378,3 +381,24 @@ def test_fused_3d_full_size_sampled(lib):
         ur, vr = P.oracle_slice(w, u[s], v[s])
         e, l2 = P.slice_errors(w, ug[s], vg[s], ur, vr)
         assert e <= P.TOL_ENERGY_F32 and l2 <= P.TOL_ENERGY_F32, (s, e, l2)
+
+
+@pytest.mark.parametrize("m_f,N", [(20, 3), (7, 1), (9, 2)])
+def test_fused_2d_xstrips_2048_depth8(lib, m_f, N):
+    """n = 2048 at depth 8 in three x-strips of 704 columns per row
+    (pr_set_wide_rows 2: 688 final columns, an 8-column halo each side; the
+    third strip overlaps the first, which alone writes the overlap): the same
+    level recurrence as the cluster rows, so bit-identical outputs, and every
+    slice against the oracle."""
+    from paper_1905_00473_gb300 import binding
+    w = W.custom_case(2, 2048, N, m_f, "f32", "inclusion", seed=60 + m_f)
+    ctx = P.make_ctx(w)
+    u, v = W.slice_states(w, seed=13)
+    binding.pr_set_wide_rows(ctx, 2)
+    ug2, vg2 = P.run_gpu(ctx, u, v, "f32")
+    binding.pr_set_wide_rows(ctx, 1)
+    ug1, vg1 = P.run_gpu(ctx, u, v, "f32")
+    assert np.array_equal(ug1, ug2) and np.array_equal(vg1, vg2)
+    for s in range(N):
+        ur, vr = P.oracle_slice(w, u[s], v[s])
+        assert P.slice_errors(w, ug2[s], vg2[s], ur, vr)[0] <= P.TOL_ENERGY_F32
