@@ -132,6 +132,9 @@ extern "C" pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void*
             for (const auto& cd : cands) {
                 const int d = cd[0], cols = cd[1];
                 if (d > 1 && !pr_tb2d_supported(b->ctx[i], d)) continue;
+                // 2048-point rows run four columns per thread whatever is set:
+                // the two-column candidates would time the same kernels again
+                if (cols == 2 && b->ctx[i]->n == 2048) continue;
                 double t = 0;
                 pr_status s = time_config(b, i, d, cols, st, &t);
                 if (s != PR_OK) {
