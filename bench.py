@@ -425,6 +425,7 @@ def run_batch(a) -> int:
         units += w.point_steps_per_sweep()
     t0 = time.perf_counter()
     batch = binding.Batch(ctxs, ui, vi, uo, vo, autotune=True)
+    mode = batch.set_mode({"chains": 0, "queue": 1, "auto": -1}[a.batch_mode])
     tune_s = time.perf_counter() - t0
     for _ in range(a.warmup):
         batch.launch()
@@ -443,11 +444,15 @@ def run_batch(a) -> int:
     # roofline of the whole graph: every instance's algorithmic traffic (20 B
     # per point per HBM pass) over the graph's time per step
     depths = [batch.info(i)[0] for i in range(len(ws))]
-    passes = [hbm_passes(w.m_f, d) for w, d in zip(ws, depths)]
+    if mode == 1:   # the queue kernel: passes of 8 levels (a lone last level splits as 5 + 4)
+        passes = [-(-(w.m_f + 1) // 8) for w in ws]
+    else:
+        passes = [hbm_passes(w.m_f, d) for w, d in zip(ws, depths)]
     step_bytes = sum(ALGO_BYTES_PER_POINT_PASS * w.points * w.n_slices * pz for w, pz in zip(ws, passes))
     peak, peak_src = measured_peak()
     achieved = step_bytes / (ms / a.steps * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": "the batch graph (every instance's passes)", "achieved": achieved,
+    roof = {"bound": "hbm", "kernel": ("batch_queue_kernel (every instance's passes)" if mode == 1 else
+                                       "the batch graph (every instance's passes)"), "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
             "algorithmic_bytes_per_launch": step_bytes, "mean_launch_ms": ms / a.steps}
     cpu = None
@@ -465,9 +470,13 @@ def run_batch(a) -> int:
                                       "depth": batch.info(i)[0], "columns": batch.info(i)[1]}
                                      for i, w in enumerate(ws)],
                        "point_updates_per_step": units, "autotune_s": tune_s,
-                       "graph": "one CUDA graph, 8 streams"},
+                       "graph": ("one CUDA graph: one persistent work-queue kernel" if mode == 1 else
+                                 "one CUDA graph: per-instance pass launches on 8 streams"),
+                       "batch_mode": {0: "chains", 1: "queue"}[mode],
+                       "batch_mode_requested": a.batch_mode},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-            "gpu_launches": a.steps * sum(passes)}   # one launch per pass in the batch graph
+            # one launch per pass in the chains graph; one in all in the queue graph
+            "gpu_launches": a.steps * (1 if mode == 1 else sum(passes))}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -752,6 +761,9 @@ def main(argv=None) -> int:
                     help="propagate only this many slices (smaller profiling runs; 0 = all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=48, help="--config 4: instances in the batch (all 48)")
+    ap.add_argument("--batch-mode", choices=["chains", "queue", "auto"], default="auto",
+                    help="--config 4: per-instance launch chains, the one work-queue kernel, or time both "
+                         "and keep the faster (default)")
     ap.add_argument("--no-parareal", action="store_true",
                     help="skip the parareal time-to-1e-4 measurement")
     ap.add_argument("--wide-rows", type=int, default=0, choices=[0, 1, 2],

@@ -365,8 +365,31 @@ pr_status pr_batch_launch(pr_batch* b, void* stream);
 
 /* pr_batch_info -- chosen block depth, fused-kernel columns per thread (0 =
  * the default; see pr_set_fused_columns) and the timed sweep (ms) of
- * instance i.  Any output pointer may be NULL. */
+ * instance i (in mode 1: depth 8 and 4 columns, the queue kernel's).  Any
+ * output pointer may be NULL. */
 pr_status pr_batch_info(const pr_batch* b, int i, int* block_depth, int* columns, double* tuned_ms);
+
+/* pr_batch_set_mode -- the form of the batch's graph (Alg. 3 parallel phase
+ * for every instance; both forms compute every instance's sweep):
+ *   0   the per-instance chains of pass launches (pr_batch_create's form);
+ *   1   ONE persistent kernel, one CTA per SM, that claims work items
+ *       (instance, pass, slice, and x-strip of 752 final columns at
+ *       n = 2048) from a device queue; pass k of a slice waits, bounded, until
+ *       every item of pass k-1 of that slice has finished.  Passes of 8
+ *       levels (a lone final level makes the last two 5 + 4), so results
+ *       agree with mode 0 to FP32 rounding, not bit for bit.  Needs every
+ *       instance 2D FP32 with n in {256, 512, 1024, 2048} and m_f >= 8
+ *       (PR_EINVAL otherwise); each switch to it builds the queue tables
+ *       from the contexts' current settings, in device memory (through the
+ *       first context's allocator);
+ *  -1   time both forms on `stream` (a warm-up and two replays each) and
+ *       keep the faster.
+ * The chosen mode is written to *chosen (may be NULL).  Synchronises the
+ * device, then re-captures the graph; the bound arrays are written by the
+ * timing replays.  In mode 1 a wait that gave up stops the queue, and
+ * pr_check then reports PR_ETIMEOUT on every instance's context (items of
+ * any instance may be left undone). */
+pr_status pr_batch_set_mode(pr_batch* b, int mode, void* stream, int* chosen);
 
 /* pr_batch_destroy -- free the graph and the streams (NULL is a no-op). */
 void pr_batch_destroy(pr_batch* b);

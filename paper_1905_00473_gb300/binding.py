@@ -76,6 +76,7 @@ _SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "pr_set_fused_columns": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_batch_destroy": (None, [_P]),
+    "pr_batch_set_mode": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int)]),
     "pr_debug_stall_waits": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_set_one_launch": (ctypes.c_int, [_P, ctypes.c_int]),
     "pr_set_resident": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -412,6 +413,14 @@ class Batch:
 
     def launch(self, stream=None):
         _check(load().pr_batch_launch(self.handle, ctypes.c_void_p(_stream_ptr(stream))), None)
+
+    def set_mode(self, mode: int, stream=None) -> int:
+        """0: per-instance launch chains, 1: one work-queue kernel, -1: time both and keep the
+        faster.  Returns the mode in effect."""
+        chosen = ctypes.c_int()
+        _check(load().pr_batch_set_mode(self.handle, int(mode), ctypes.c_void_p(_stream_ptr(stream)),
+                                        ctypes.byref(chosen)), None)
+        return chosen.value
 
     def info(self, i):
         """(block depth, fused columns per thread (0 = the default), tuned ms) of instance i."""

@@ -1,8 +1,12 @@
 // Batches of independent problem instances of uneven sizes (one parareal
-// iteration's fine sweep per instance, Alg. 3 parFor, for many instances):
-// per-instance block depth and fused-kernel geometry chosen by timing, then
-// every instance's sweep
-// captured into one CUDA graph whose branches run on several streams.
+// iteration's fine sweep per instance, Alg. 3 parFor, for many instances),
+// replayed as one CUDA graph in one of two forms:
+//   mode 0  per-instance block depth and fused-kernel geometry chosen by
+//           timing, every instance's chain of pass launches a branch of the
+//           graph, the branches spread over several streams;
+//   mode 1  one persistent kernel that claims every (instance, pass, slice,
+//           x-strip) item from a device queue (batch_queue.cu).
+// pr_batch_set_mode switches between them, or times both and keeps the faster.
 #include <stdio.h>
 
 #include <algorithm>
@@ -21,6 +25,8 @@ struct pr_batch {
     std::vector<cudaEvent_t> ev;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int mode = 0;                 // 0 per-instance launch chains, 1 the work-queue kernel
+    pr_queue* queue = nullptr;    // built on the first switch to mode 1
     std::string err;
 };
 
@@ -32,6 +38,7 @@ void destroy(pr_batch* b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    pr_queue_destroy(b->queue);
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     delete b;
@@ -59,6 +66,68 @@ pr_status time_config(pr_batch* b, int i, int d, int cols, cudaStream_t st, doub
     if (s != PR_OK) return s;
     if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "pr_batch: timing");
     *ms = t;
+    return PR_OK;
+}
+
+// (Re)capture the batch's graph in its current mode.
+pr_status capture(pr_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    const int count = (int)b->ctx.size();
+    cudaStream_t cap = b->streams[kStreams];
+    cudaEvent_t fork = b->ev[kStreams];
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "pr_batch: begin capture");
+    pr_status ps = PR_OK;
+    if (b->mode == 1) {
+        ps = pr_queue_launch(b->queue, cap);
+    } else {
+        // fork on kStreams streams, one branch per instance, join; biggest
+        // instances first, spread over the streams
+        cudaEventRecord(fork, cap);
+        std::vector<int> order(count);
+        for (int i = 0; i < count; ++i) order[i] = i;
+        std::sort(order.begin(), order.end(), [&](int a, int c) {
+            return (double)b->ctx[a]->pts * b->ctx[a]->N * b->ctx[a]->m_f >
+                   (double)b->ctx[c]->pts * b->ctx[c]->N * b->ctx[c]->m_f;
+        });
+        for (int k = 0; k < kStreams; ++k) cudaStreamWaitEvent(b->streams[k], fork, 0);
+        for (int j = 0; j < count && ps == PR_OK; ++j) {
+            const int i = order[j];
+            ps = pr_fine_all_slices(b->ctx[i], b->ui[i], b->vi[i], b->uo[i], b->vo[i], 0, b->ctx[i]->N,
+                                    b->streams[j % kStreams]);
+        }
+        for (int k = 0; k < kStreams; ++k) {
+            cudaEventRecord(b->ev[k], b->streams[k]);
+            cudaStreamWaitEvent(cap, b->ev[k], 0);
+        }
+    }
+    e = cudaStreamEndCapture(cap, &b->graph);
+    if (ps != PR_OK) return ps;
+    if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "pr_batch: end capture");
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "pr_batch: instantiate");
+    return PR_OK;
+}
+
+// time `reps` replays of the batch's graph on st, after one warm-up replay
+pr_status time_graph(pr_batch* b, cudaStream_t st, int reps, double* ms) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t e = cudaGraphLaunch(b->exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(b->exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "pr_batch: timing");
+    *ms = t / reps;
     return PR_OK;
 }
 
@@ -154,7 +223,7 @@ extern "C" pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void*
             b->ms[i] = best;
         }
     }
-    // capture: fork on kStreams streams, one branch per instance, join
+    // streams of the graph's branches, the fork event and the capture stream
     for (int k = 0; k < kStreams; ++k) {
         cudaStream_t s;
         cudaEvent_t e;
@@ -167,43 +236,18 @@ extern "C" pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void*
         b->ev.push_back(e);
     }
     cudaEvent_t fork;
-    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    b->ev.push_back(fork);
     cudaStream_t cap;
-    cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        destroy(b);
+        return pr_fail(nullptr, PR_ECUDA, "pr_batch_create: stream/event creation");
+    }
+    b->ev.push_back(fork);
     b->streams.push_back(cap);
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) {
+    const pr_status ps = capture(b);
+    if (ps != PR_OK) {
         destroy(b);
-        return pr_cuda_fail(nullptr, e, "pr_batch_create: begin capture");
-    }
-    cudaEventRecord(fork, cap);
-    // biggest instances first, spread over the streams
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int a, int c) {
-        return (double)b->ctx[a]->pts * b->ctx[a]->N * b->ctx[a]->m_f > (double)b->ctx[c]->pts * b->ctx[c]->N * b->ctx[c]->m_f;
-    });
-    for (int k = 0; k < kStreams; ++k) cudaStreamWaitEvent(b->streams[k], fork, 0);
-    pr_status ps = PR_OK;
-    for (int j = 0; j < count && ps == PR_OK; ++j) {
-        const int i = order[j];
-        ps = pr_fine_all_slices(b->ctx[i], b->ui[i], b->vi[i], b->uo[i], b->vo[i], 0, b->ctx[i]->N,
-                                b->streams[j % kStreams]);
-    }
-    for (int k = 0; k < kStreams; ++k) {
-        cudaEventRecord(b->ev[k], b->streams[k]);
-        cudaStreamWaitEvent(cap, b->ev[k], 0);
-    }
-    e = cudaStreamEndCapture(cap, &b->graph);
-    if (ps != PR_OK || e != cudaSuccess) {
-        destroy(b);
-        return ps != PR_OK ? ps : pr_cuda_fail(nullptr, e, "pr_batch_create: end capture");
-    }
-    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-    if (e != cudaSuccess) {
-        destroy(b);
-        return pr_cuda_fail(nullptr, e, "pr_batch_create: instantiate");
+        return ps;
     }
     *out = b;
     return PR_OK;
@@ -219,9 +263,55 @@ extern "C" pr_status pr_batch_launch(pr_batch* b, void* stream) {
 extern "C" pr_status pr_batch_info(const pr_batch* b, int i, int* block_depth, int* columns,
                                    double* tuned_ms) {
     if (!b || i < 0 || i >= (int)b->ctx.size()) return pr_fail(nullptr, PR_EINVAL, "pr_batch_info: bad index");
-    if (block_depth) *block_depth = b->depth[i];
-    if (columns) *columns = b->cols[i];
+    // the work-queue kernel runs every instance at depth 8, four columns a thread
+    if (block_depth) *block_depth = b->mode == 1 ? 8 : b->depth[i];
+    if (columns) *columns = b->mode == 1 ? 4 : b->cols[i];
     if (tuned_ms) *tuned_ms = b->ms[i];
+    return PR_OK;
+}
+
+extern "C" pr_status pr_batch_set_mode(pr_batch* b, int mode, void* stream, int* chosen) {
+    if (!b || !b->exec) return pr_fail(nullptr, PR_EINVAL, "pr_batch_set_mode: no batch");
+    if (mode < -1 || mode > 1) return pr_fail(nullptr, PR_EINVAL, "pr_batch_set_mode: mode must be -1, 0 or 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    // replays of the graph that is about to be replaced may still be in flight
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "pr_batch_set_mode: synchronize");
+    if (mode != 0) {
+        // the queue tables, rebuilt from the contexts' current settings
+        const int count = (int)b->ctx.size();
+        pr_queue* q = nullptr;
+        pr_status s = pr_queue_create(count, b->ctx.data(), b->ui.data(), b->vi.data(), b->uo.data(), b->vo.data(),
+                                      &q);
+        if (s != PR_OK) return s;
+        if (b->mode == 1) {
+            // the current graph launches the old tables: replace it first
+            b->mode = 0;
+            s = capture(b);
+            if (s != PR_OK) {
+                pr_queue_destroy(q);
+                return s;
+            }
+        }
+        pr_queue_destroy(b->queue);
+        b->queue = q;
+    }
+    int pick = mode;
+    if (mode == -1) {
+        // time both forms (two replays each, after a warm-up) and keep the faster
+        double t[2] = {0.0, 0.0};
+        for (int m = 0; m < 2; ++m) {
+            b->mode = m;
+            pr_status s = capture(b);
+            if (s == PR_OK) s = time_graph(b, st, 2, &t[m]);
+            if (s != PR_OK) return s;
+        }
+        pick = t[1] < t[0] ? 1 : 0;
+    }
+    b->mode = pick;
+    pr_status s = capture(b);
+    if (s != PR_OK) return s;
+    if (chosen) *chosen = pick;
     return PR_OK;
 }
 

@@ -236,6 +236,18 @@ bool pr_tb2d_sweep_supported(const pr_ctx* ctx, int passes);
 // 3D FP32 temporally blocked kernel (fine_tb3d.cu): passes of 2..4 levels
 bool pr_tb3d_supported(const pr_ctx* ctx, int depth);
 
+// ---- the batch as one persistent work-queue kernel (batch_queue.cu) ----------
+// Every fused pass of every slice (x-strip at n = 2048) of every instance is
+// an item of a device queue claimed by one CTA per SM; pass k of a slice
+// waits (bounded) for all items of pass k - 1 of that slice.  Instances: 2D
+// FP32, n in {256, 512, 1024, 2048}, m_f >= 8, a bfloat16 residual scratch.
+struct pr_queue;
+bool pr_queue_supported(const pr_ctx* c);
+pr_status pr_queue_create(int count, pr_ctx* const* ctx, const void* const* ui, const void* const* vi,
+                          void* const* uo, void* const* vo, pr_queue** out);
+pr_status pr_queue_launch(pr_queue* q, cudaStream_t st);   // counter reset + one launch; capturable
+void pr_queue_destroy(pr_queue* q);
+
 // ---- whole slices in one cluster's shared memory (resident2d.cu) ------------
 // 2D FP32 grids up to 256^2 at block depth 8: all m + 1 kicks of each slice in
 // one launch (a cluster of 8 CTAs per slice), bit-identical to the per-pass

@@ -215,6 +215,21 @@ __device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, un
     }
 }
 
+// OR of v over threads 0 .. GB-1 (whole warps, all executing this barrier),
+// at the named barrier 1: the per-row barrier of a thread group that holds
+// its rows alone inside a larger CTA.
+template <int GB>
+__device__ __forceinline__ bool group_or(int v) {
+    static_assert(GB % 32 == 0, "a named barrier counts whole warps");
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(v), "n"(GB)
+        : "memory");
+    return r != 0;
+}
+
 // One pipeline step at ring position q = sg.base + i with K = q mod kU.
 // Register rings per level l (period 3, K mod 3 selects the slots):
 //   R[l][.]  du rows of level l's input: centre = K%3, south = (K+2)%3,
@@ -222,7 +237,7 @@ __device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, un
 //   VV[l][.] u_t of level l's input row: read (K+2)%3, written K%3
 // `par` is the mbarrier phase parity of the current ring lap.  Returns true
 // when some thread's bounded wait gave up.
-template <int NT, int B, int XH, bool MID, bool HALF0, int CL, int K, bool SWEEP>
+template <int NT, int B, int XH, bool MID, bool HALF0, int CL, int K, bool SWEEP, int GB>
 __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, unsigned char* sm, int i,
                                           uint32_t par, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
                                           float (&UH)[3][kCpt], float (&KR)[kU][kCpt], float (&DR)[kU][kCpt],
@@ -580,7 +595,8 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
         }
     }
     // one barrier per row; it also makes the abort decision uniform
-    return __syncthreads_or(timed_out) != 0;
+    if constexpr (GB == 0) return __syncthreads_or(timed_out) != 0;
+    else return group_or<GB>(timed_out);
 }
 
 // XH = 0: a CTA holds whole periodic rows (n = 4 NT).  XH > 0: it holds
@@ -609,12 +625,18 @@ __device__ __forceinline__ void tb2d_init_bars(unsigned char* sm) {
     __syncthreads();
 }
 
-// One pass of B levels (or p.levels in the general variant) over the CTA's
-// share of the rows, continuing the ring at position `pos` (a multiple of kU;
-// advanced past the pass).  Returns true if a bounded wait gave up.
-template <int NT, int B, int XH, bool MID, bool HALF0, int CL, bool SWEEP>
-__device__ __forceinline__ bool tb2d_pass(const Tb2dParams& p, unsigned char* sm, uint32_t& pos_io, bool skip) {
+// One pass of B levels (or p.levels in the general variant) over the rows
+// [r_begin, r_end) of the pass's row space (rows_total = slices x strips x
+// n), continuing the ring at position `pos` (a multiple of kU; advanced past
+// the pass).  Run by threads 0 .. NT-1 of the CTA: GB = 0, the whole CTA,
+// which is NT threads; GB = NT, the first NT threads (whole warps) of a larger
+// CTA, whose per-row barrier is then the named barrier 1.  Returns true if a
+// bounded wait gave up.
+template <int NT, int B, int XH, bool MID, bool HALF0, int CL, bool SWEEP, int GB>
+__device__ __forceinline__ bool tb2d_rows(const Tb2dParams& p, unsigned char* sm, uint32_t& pos_io, int64_t r_begin,
+                                          int64_t r_end) {
     static_assert(CL == 1 || (CL == 2 && XH == 0), "rows are shared by at most two CTAs, without x-strips");
+    static_assert(GB == 0 || (GB == NT && CL == 1), "a thread group holds whole rows or x-strips alone");
     using S = Smem<NT, B>;
     const int t = threadIdx.x;
     const int n = p.n;
@@ -631,11 +653,6 @@ __device__ __forceinline__ bool tb2d_pass(const Tb2dParams& p, unsigned char* sm
     Pols pol = {0, 0, 0};
     if (t == 0) pol = {policy(0), policy(1), policy(2)};
 
-    // per-CTA (per-cluster) row ranges of equal cost: rows + (L + B) steps
-    // per segment
-    const int64_t unit = blockIdx.x / CL, units = gridDim.x / CL;
-    const int64_t r_begin = skip ? 0 : balanced_row(p.rows_total, n, L + B, unit, units);
-    const int64_t r_end = skip ? 0 : balanced_row(p.rows_total, n, L + B, unit + 1, units);
     // ring positions: a segment occupies [base, base + niter) and the next one
     // starts at the following multiple of kU; positions that receive no
     // copy get a plain arrival, so slot s completes its phase j at position
@@ -697,7 +714,7 @@ __device__ __forceinline__ bool tb2d_pass(const Tb2dParams& p, unsigned char* sm
         int i = 0;
 #define PR_TB2D_STEP(K)                                                                                   \
     if (i >= niter) break;                                                                                 \
-    if (tb2d_step<NT, B, XH, MID, HALF0, CL, K, SWEEP>(p, sg, sm, i, par, R, VV, UH, KR, DR, timed_out, consumed, \
+    if (tb2d_step<NT, B, XH, MID, HALF0, CL, K, SWEEP, GB>(p, sg, sm, i, par, R, VV, UH, KR, DR, timed_out, consumed, \
                                                issued_end, pol, pr)) {                                     \
         aborted = true;                                                                                    \
         break;                                                                                             \
@@ -740,6 +757,17 @@ __device__ __forceinline__ bool tb2d_pass(const Tb2dParams& p, unsigned char* sm
     }
     pos_io = pos;
     return aborted;
+}
+
+// One pass over this CTA's (cluster's) share of the rows of the whole pass:
+// contiguous ranges of equal cost, rows + (L + B) steps per segment.
+template <int NT, int B, int XH, bool MID, bool HALF0, int CL, bool SWEEP>
+__device__ __forceinline__ bool tb2d_pass(const Tb2dParams& p, unsigned char* sm, uint32_t& pos_io, bool skip) {
+    const int L = MID ? B : p.levels;
+    const int64_t unit = blockIdx.x / CL, units = gridDim.x / CL;
+    const int64_t r_begin = skip ? 0 : balanced_row(p.rows_total, p.n, L + B, unit, units);
+    const int64_t r_end = skip ? 0 : balanced_row(p.rows_total, p.n, L + B, unit + 1, units);
+    return tb2d_rows<NT, B, XH, MID, HALF0, CL, SWEEP, 0>(p, sm, pos_io, r_begin, r_end);
 }
 
 template <int NT, int B, int XH, bool MID, bool HALF0, int CL>

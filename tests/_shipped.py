@@ -46,3 +46,23 @@ def balanced_rows(queries):
     vals = [int(x) for x in res.stdout.split()]
     assert len(vals) == len(queries)
     return vals
+
+
+def queue_plan(instances):
+    """qplan::build of queue_plan.h for instances [(n, slices, m)], evaluated
+    by the compiled harness: (counters, passes, items), passes as tuples
+    (inst, k, cls, g0, levels, strips) and items as (pass, vslice, dep, need)
+    in queue order; counters is -1 if the plan was refused."""
+    text = "".join(f"{n} {s} {m}\n" for n, s, m in instances)
+    res = subprocess.run([harness(), "plan"], input=text, capture_output=True, text=True, check=True)
+    ndep, passes, items = None, [], []
+    for line in res.stdout.splitlines():
+        tag, *vals = line.split()
+        vals = [int(v) for v in vals]
+        if tag == "D":
+            ndep = vals[0]
+        elif tag == "P":
+            passes.append(tuple(vals))
+        elif tag == "I":
+            items.append(tuple(vals))
+    return ndep, passes, items
