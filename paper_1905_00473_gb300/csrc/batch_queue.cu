@@ -41,19 +41,23 @@
 
 namespace {
 
-constexpr int kQT = 256;               // threads of a queue CTA
+constexpr int kQT = qplan::kThreads;   // threads of a queue CTA
 constexpr int kQB = qplan::kDepth;     // block depth of the queued passes
 static_assert(qplan::kCols == kCpt, "the plan's strip widths are those of the pass body");
 
+// A class's thread groups: NT threads each, G side by side, each with its own
+// `stride` bytes of shared memory (the pass body's layout, 128-byte aligned).
 template <int C>
 struct QCls {
     static constexpr int NT = qplan::kClasses[C].nt, XH = qplan::kClasses[C].xh, n = qplan::kClasses[C].n;
-    static_assert(NT % 32 == 0 && NT <= kQT, "a class's thread group is whole warps of the CTA");
+    static constexpr int G = qplan::kClasses[C].groups;
+    static constexpr uint32_t stride = (Smem<NT, kQB>::total + 127u) / 128u * 128u;
+    static_assert(NT % 32 == 0 && G * NT <= kQT, "a class's thread groups are whole warps of the CTA");
 };
-
-constexpr uint32_t kQSmem = Smem<256, kQB>::total;
-static_assert(Smem<64, kQB>::total <= kQSmem && Smem<128, kQB>::total <= kQSmem && Smem<192, kQB>::total <= kQSmem,
-              "the whole-row 1024 layout is the largest");
+constexpr uint32_t qmax(uint32_t a, uint32_t b) { return a > b ? a : b; }
+constexpr uint32_t kQSmem = qmax(qmax(QCls<0>::G * QCls<0>::stride, QCls<1>::G * QCls<1>::stride),
+                                 qmax(QCls<2>::G * QCls<2>::stride, QCls<3>::G * QCls<3>::stride));
+static_assert(kQSmem <= 227u * 1024u, "a queue CTA's shared memory fits an SM");
 
 struct QPass {
     Tb2dParams p;
@@ -68,14 +72,19 @@ struct QItem {
     unsigned need;   // completions of that counter before the item may start
 };
 
+struct QUnit {
+    int first, count;   // items first .. first + count - 1, one pass, one per thread group
+};
+
 struct QParams {
     const QItem* items;
+    const QUnit* units;
     const QPass* passes;
-    unsigned* head;   // next unclaimed item (zero at launch)
+    unsigned* head;   // next unclaimed unit (zero at launch)
     unsigned* done;   // per (instance, slice): items finished (zero at launch)
     int* stop;        // set when a wait gave up: nothing more is claimed (zero at launch)
     int* const* flags;   // every instance's error flag
-    int nitems, ninst;
+    int nunits, ninst;
     uint64_t wait_ns;
 };
 
@@ -86,10 +95,11 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
 template <int C>
 __device__ __forceinline__ void q_bars(unsigned char* sm, bool arm) {
     using S = Smem<QCls<C>::NT, kQB>;
-    for (int s = 0; s < kU; ++s) {
-        if (arm) mbar_init(S::bar(sm, s), 1);
-        else mbar_inval(S::bar(sm, s));
-    }
+    for (int g = 0; g < QCls<C>::G; ++g)
+        for (int s = 0; s < kU; ++s) {
+            if (arm) mbar_init(S::bar(sm + g * QCls<C>::stride, s), 1);
+            else mbar_inval(S::bar(sm + g * QCls<C>::stride, s));
+        }
 }
 __device__ __forceinline__ void q_bars_of(unsigned char* sm, int c, bool arm) {
     switch (c) {
@@ -132,36 +142,56 @@ __device__ __forceinline__ bool q_wait(const unsigned* ctr, unsigned need, uint6
 // the two widest classes, which carry nearly all of a mixed batch's work; the
 // general body for every other pass (it takes the half kicks at g = 0 and
 // g = m, and passes of fewer levels), which keeps the kernel to six bodies.
+// The whole-sweep form of the body (SWEEP = 1: the finished row's u_hi read
+// past L1, kappa read per level: with the pass parameters in registers the
+// kappa register ring would spill).  Run by thread group `grp` on its own
+// shared memory.
 template <int C>
-__device__ __forceinline__ bool q_run(const Tb2dParams& p, int variant, unsigned char* sm, uint32_t& pos, int vslice) {
+__device__ __forceinline__ bool q_run(const Tb2dParams& p, int variant, unsigned char* sm, uint32_t& pos, int vslice,
+                                      int grp) {
     constexpr int NT = QCls<C>::NT, XH = QCls<C>::XH;
     const int64_t r0 = (int64_t)vslice * QCls<C>::n, r1 = r0 + QCls<C>::n;
+    unsigned char* gsm = sm + grp * QCls<C>::stride;
     if constexpr (C >= 2) {
-        if (variant == 1) return tb2d_rows<NT, kQB, XH, true, false, 1, true, NT>(p, sm, pos, r0, r1);
+        if (variant == 1) return tb2d_rows<NT, kQB, XH, true, false, 1, 1, NT>(p, gsm, pos, r0, r1, grp);
     }
-    return tb2d_rows<NT, kQB, XH, false, false, 1, true, NT>(p, sm, pos, r0, r1);
+    return tb2d_rows<NT, kQB, XH, false, false, 1, 1, NT>(p, gsm, pos, r0, r1, grp);
+}
+
+template <int C>
+__device__ __forceinline__ bool q_group(const QParams& qp, const QUnit& un, const Tb2dParams& p, int variant,
+                                        unsigned char* sm, uint32_t& pos) {
+    if constexpr (QCls<C>::G == 1) {
+        if ((int)threadIdx.x >= QCls<C>::NT) return false;   // idle for the unit
+        return q_run<C>(p, variant, sm, pos, qp.items[un.first].vslice, 0);
+    } else {
+        const int g = (int)threadIdx.x / QCls<C>::NT;   // this thread's group; g >= count: idle for the unit
+        if (g >= un.count) return false;
+        return q_run<C>(p, variant, sm, pos, qp.items[un.first + g].vslice, g);
+    }
 }
 
 __global__ void __launch_bounds__(kQT, 1) batch_queue_kernel(const QParams qp) {
     extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ int s_item;
-    __shared__ uint32_t s_pos;
+    __shared__ int s_unit;
     int cls = -1;
+    // ring position of this thread's group: the same in every thread of a
+    // group, which runs the same items
     uint32_t pos = 0;
     for (;;) {
         if (threadIdx.x == 0) {
-            int q = -1;
+            int u = -1;
             if (*(volatile int*)qp.stop == 0) {
                 const unsigned h = atomicAdd(qp.head, 1u);
-                if (h < (unsigned)qp.nitems) q = (int)h;
+                if (h < (unsigned)qp.nunits) u = (int)h;
             }
-            s_item = q;
+            s_unit = u;
         }
         __syncthreads();
-        const int q = s_item;
-        if (q < 0) break;
-        const QItem it = qp.items[q];
-        const QPass* qd = qp.passes + it.pass;
+        const int u = s_unit;
+        if (u < 0) break;
+        const QUnit un = qp.units[u];
+        const QPass* qd = qp.passes + qp.items[un.first].pass;
         const int c = qd->cls;
         if (c != cls) {
             q_switch(sm, cls, c);
@@ -170,7 +200,10 @@ __global__ void __launch_bounds__(kQT, 1) batch_queue_kernel(const QParams qp) {
         }
         int ok = 1;
         if (threadIdx.x == 0) {
-            ok = q_wait(qp.done + it.dep, it.need, qp.wait_ns);
+            for (int j = 0; j < un.count && ok; ++j) {
+                const QItem it = qp.items[un.first + j];
+                ok = q_wait(qp.done + it.dep, it.need, qp.wait_ns);
+            }
             if (!ok) {
                 atomicExch(qd->p.flag, 1);
                 atomicExch(qp.stop, 1);
@@ -179,30 +212,29 @@ __global__ void __launch_bounds__(kQT, 1) batch_queue_kernel(const QParams qp) {
             asm volatile("fence.proxy.async.global;" ::: "memory");
         }
         if (!__syncthreads_and(ok)) break;
+        // the pass parameters in registers (they spill ~100 bytes; read from
+        // shared memory where used instead, the 2048 strips ran 9 % slower)
         const Tb2dParams p = qd->p;
         // an instance whose earlier work gave up (flag not yet read by
         // pr_check) skips its items, which still count as done
         const bool skip = *(volatile int*)p.flag != 0;
-        const int group = c == 0 ? QCls<0>::NT : c == 1 ? QCls<1>::NT : c == 2 ? QCls<2>::NT : QCls<3>::NT;
         bool ab = false;
-        if (!skip && (int)threadIdx.x < group) {
+        if (!skip) {
             switch (c) {
-                case 0: ab = q_run<0>(p, qd->variant, sm, pos, it.vslice); break;
-                case 1: ab = q_run<1>(p, qd->variant, sm, pos, it.vslice); break;
-                case 2: ab = q_run<2>(p, qd->variant, sm, pos, it.vslice); break;
-                default: ab = q_run<3>(p, qd->variant, sm, pos, it.vslice); break;
+                case 0: ab = q_group<0>(qp, un, p, qd->variant, sm, pos); break;
+                case 1: ab = q_group<1>(qp, un, p, qd->variant, sm, pos); break;
+                case 2: ab = q_group<2>(qp, un, p, qd->variant, sm, pos); break;
+                default: ab = q_group<3>(qp, un, p, qd->variant, sm, pos); break;
             }
         }
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        if (threadIdx.x == 0) s_pos = pos;
         if (__syncthreads_or(ab)) {
             if (threadIdx.x == 0) atomicExch(qp.stop, 1);
             break;
         }
-        pos = s_pos;
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(qp.done + it.dep, 1u);
+            for (int j = 0; j < un.count; ++j) atomicAdd(qp.done + qp.items[un.first + j].dep, 1u);
         }
     }
     // a queue that stopped early left items of any instance undone: every
@@ -217,13 +249,14 @@ struct pr_queue {
     pr_ctx* owner = nullptr;   // the first instance's context: its allocator holds the tables
     int device = 0;
     QItem* items = nullptr;
+    QUnit* units = nullptr;
     QPass* passes = nullptr;
     unsigned* ctr = nullptr;   // head, then one counter per (instance, slice)
     int* stop = nullptr;
     int** flags = nullptr;
     int ninst = 0;
     size_t ctr_bytes = 0;
-    int nitems = 0;
+    int nunits = 0;
     int grid = 0;
     uint64_t wait_ns = 0;
 };
@@ -236,6 +269,7 @@ bool pr_queue_supported(const pr_ctx* c) {
 void pr_queue_destroy(pr_queue* q) {
     if (!q) return;
     pr_dev_free(q->owner, q->items);
+    pr_dev_free(q->owner, q->units);
     pr_dev_free(q->owner, q->passes);
     pr_dev_free(q->owner, q->ctr);
     pr_dev_free(q->owner, q->stop);
@@ -258,7 +292,8 @@ pr_status pr_queue_create(int count, pr_ctx* const* ctx, const void* const* ui, 
     }
     std::vector<qplan::Pass> plan;
     std::vector<qplan::Item> qitems;
-    const int ndep = qplan::build(inst, &plan, &qitems);
+    std::vector<qplan::Unit> qunits;
+    const int ndep = qplan::build(inst, &plan, &qitems, &qunits);
     if (ndep < 0) return pr_fail(nullptr, PR_EINVAL, "pr_batch (queue): no plan");
     std::vector<QPass> passes;
     for (const qplan::Pass& pl : plan) {
@@ -292,14 +327,18 @@ pr_status pr_queue_create(int count, pr_ctx* const* ctx, const void* const* ui, 
     std::vector<QItem> items;
     items.reserve(qitems.size());
     for (const qplan::Item& it : qitems) items.push_back({it.pass, it.vslice, it.dep, it.need});
+    std::vector<QUnit> units;
+    units.reserve(qunits.size());
+    for (const qplan::Unit& un : qunits) units.push_back({un.first, un.count});
 
     pr_queue* q = new pr_queue();
     q->owner = ctx[0];
     cudaGetDevice(&q->device);
-    q->nitems = (int)items.size();
+    q->nunits = (int)units.size();
     q->wait_ns = wait_ns;
     q->ctr_bytes = (1 + (size_t)ndep) * sizeof(unsigned);
     cudaError_t e = pr_dev_malloc(q->owner, (void**)&q->items, items.size() * sizeof(QItem));
+    if (e == cudaSuccess) e = pr_dev_malloc(q->owner, (void**)&q->units, units.size() * sizeof(QUnit));
     if (e == cudaSuccess) e = pr_dev_malloc(q->owner, (void**)&q->passes, passes.size() * sizeof(QPass));
     if (e == cudaSuccess) e = pr_dev_malloc(q->owner, (void**)&q->ctr, q->ctr_bytes);
     if (e == cudaSuccess) e = pr_dev_malloc(q->owner, (void**)&q->stop, sizeof(int));
@@ -310,6 +349,8 @@ pr_status pr_queue_create(int count, pr_ctx* const* ctx, const void* const* ui, 
     if (e == cudaSuccess) e = cudaMemcpy(q->flags, flags.data(), count * sizeof(int*), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(q->items, items.data(), items.size() * sizeof(QItem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(q->units, units.data(), units.size() * sizeof(QUnit), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(q->passes, passes.data(), passes.size() * sizeof(QPass), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -333,12 +374,13 @@ pr_status pr_queue_launch(pr_queue* q, cudaStream_t st) {
     if (e != cudaSuccess) return pr_cuda_fail(nullptr, e, "pr_batch (queue): clear counters");
     QParams qp;
     qp.items = q->items;
+    qp.units = q->units;
     qp.passes = q->passes;
     qp.head = q->ctr;
     qp.done = q->ctr + 1;
     qp.stop = q->stop;
     qp.flags = q->flags;
-    qp.nitems = q->nitems;
+    qp.nunits = q->nunits;
     qp.ninst = q->ninst;
     qp.wait_ns = q->wait_ns;
     batch_queue_kernel<<<q->grid, kQT, kQSmem, st>>>(qp);

@@ -11,16 +11,18 @@
 
 namespace qplan {
 
-constexpr int kDepth = 8;   // levels of a full queued pass
-constexpr int kCols = 4;    // grid columns per thread
+constexpr int kDepth = 8;      // levels of a full queued pass
+constexpr int kCols = 4;       // grid columns per thread
+constexpr int kThreads = 256;  // threads of a queue CTA
 
-// Width classes: the thread group that holds one item's rows, and the x-halo
-// of its strips (0: whole periodic rows).  n = 2048 runs x-strips of
-// 4 * 192 = 768 columns, 752 of them final.
+// Width classes: the thread group that holds one item's rows, the x-halo of
+// its strips (0: whole periodic rows), and the groups a CTA runs side by side
+// (one item each).  n = 2048 runs x-strips of 4 * 192 = 768 columns, 752 of
+// them final.
 struct Cls {
-    int n, nt, xh;
+    int n, nt, xh, groups;
 };
-constexpr Cls kClasses[4] = {{256, 64, 0}, {512, 128, 0}, {1024, 256, 0}, {2048, 192, 8}};
+constexpr Cls kClasses[4] = {{256, 64, 0, 4}, {512, 128, 0, 2}, {1024, 256, 0, 1}, {2048, 192, 8, 1}};
 
 inline int class_of(int64_t n) {
     for (int c = 0; c < 4; ++c)
@@ -66,16 +68,24 @@ struct Item {
     int dep;         // completion counter of the item's (instance, slice)
     unsigned need;   // completions of that counter before the item may start
 };
+// What one CTA claims: items first .. first + count - 1 (one pass), one per
+// thread group of the pass's class.
+struct Unit {
+    int first, count;
+};
 
 // Passes of every instance, and the items in queue order: pass k of an
 // instance of P passes has the key (k + 1/2) / P (instances interleaved by
-// progress; ties keep instance order), then its slices and strips in order.
-// Pass k of a slice needs k * strips completions of the slice's counter, one
-// per item of each earlier pass.  Returns the number of counters, or -1 if
-// an instance has no class or fewer than 8 steps.
-inline int build(const std::vector<Inst>& inst, std::vector<Pass>* passes, std::vector<Item>* items) {
+// progress; ties keep instance order), then its slices and strips in order,
+// cut into units of the class's group count.  Pass k of a slice needs
+// k * strips completions of the slice's counter, one per item of each
+// earlier pass.  Returns the number of counters, or -1 if an instance has no
+// class or fewer than 8 steps.
+inline int build(const std::vector<Inst>& inst, std::vector<Pass>* passes, std::vector<Item>* items,
+                 std::vector<Unit>* units) {
     passes->clear();
     items->clear();
+    units->clear();
     struct Key {
         double key;
         int pass;
@@ -98,9 +108,12 @@ inline int build(const std::vector<Inst>& inst, std::vector<Pass>* passes, std::
     std::stable_sort(order.begin(), order.end(), [](const Key& a, const Key& b) { return a.key < b.key; });
     for (const Key& o : order) {
         const Pass& p = (*passes)[o.pass];
+        const int first = (int)items->size();
         for (int s = 0; s < inst[p.inst].slices; ++s)
             for (int x = 0; x < p.strips; ++x)
                 items->push_back({o.pass, s * p.strips + x, dep_base[o.pass] + s, (unsigned)(p.k * p.strips)});
+        const int end = (int)items->size(), g = kClasses[p.cls].groups;
+        for (int a = first; a < end; a += g) units->push_back({a, std::min(g, end - a)});
     }
     return ndep;
 }

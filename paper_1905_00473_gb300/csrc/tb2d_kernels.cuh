@@ -215,18 +215,26 @@ __device__ __forceinline__ void issue_row(const Tb2dParams& p, const Seg& sg, un
     }
 }
 
-// OR of v over threads 0 .. GB-1 (whole warps, all executing this barrier),
-// at the named barrier 1: the per-row barrier of a thread group that holds
-// its rows alone inside a larger CTA.
+// OR of v over the GB threads of a thread group (whole warps, all executing
+// this barrier), at the named barrier `id` (1 + the group's index): the
+// per-row barrier of a group that holds its rows alone inside a larger CTA.
 template <int GB>
-__device__ __forceinline__ bool group_or(int v) {
+__device__ __forceinline__ bool group_or(int v, int id) {
     static_assert(GB % 32 == 0, "a named barrier counts whole warps");
     int r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"(v), "n"(GB)
-        : "memory");
+    if (id == 1) {   // the first group (the only one of single-group CTAs): an immediate barrier id
+        asm volatile(
+            "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+            : "=r"(r)
+            : "r"(v), "n"(GB)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+            : "=r"(r)
+            : "r"(v), "r"(id), "n"(GB)
+            : "memory");
+    }
     return r != 0;
 }
 
@@ -237,18 +245,18 @@ __device__ __forceinline__ bool group_or(int v) {
 //   VV[l][.] u_t of level l's input row: read (K+2)%3, written K%3
 // `par` is the mbarrier phase parity of the current ring lap.  Returns true
 // when some thread's bounded wait gave up.
-template <int NT, int B, int XH, bool MID, bool HALF0, int CL, int K, bool SWEEP, int GB>
+template <int NT, int B, int XH, bool MID, bool HALF0, int CL, int K, int SWEEP, int GB>
 __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, unsigned char* sm, int i,
                                           uint32_t par, float (&R)[B][3][kCpt], float (&VV)[B][3][kCpt],
                                           float (&UH)[3][kCpt], float (&KR)[kU][kCpt], float (&DR)[kU][kCpt],
                                           int& timed_out, uint32_t& consumed, uint32_t& issued_end,
-                                          const Pols& pol, Pair& pr) {
+                                          const Pols& pol, Pair& pr, int grp) {
     using S = Smem<NT, B>;
     constexpr int W = S::W;
     constexpr int CUR = K % 3, PRV = (K + 2) % 3, NXT = (K + 1) % 3;
     constexpr uint32_t SQ = K % kRS, S1 = (K + kRS - 1) % kRS, S2 = (K + kRS - 2) % kRS;
     constexpr uint32_t SN = (K + kPre) % kRS;
-    const int t = threadIdx.x;
+    const int t = GB == 0 ? (int)threadIdx.x : (int)threadIdx.x - grp * GB;
     const int n = p.n;
     const int L = MID ? B : sg.L;
 
@@ -287,10 +295,10 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
     float4 u0o = make_float4(0.f, 0.f, 0.f, 0.f);
     if (do_out) {
         off_out = sg.slice_off + (int64_t)seg_row(sg.ylo, rho_out, n) * n + sg.x0 + kCpt * t;
-        if constexpr (SWEEP) {
-            // in a whole-sweep launch the input was written by other CTAs in
-            // the previous pass: read it from L2, past this SM's L1, marked
-            // evict-first there like the streamed rows
+        if constexpr (SWEEP != 0) {
+            // in a whole-sweep or work-queue launch the input was written by
+            // other CTAs earlier in the launch: read it from L2, past this
+            // SM's L1, marked evict-first there like the streamed rows
             const uint64_t ef = policy(0);
             asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
                          : "=f"(u0o.x), "=f"(u0o.y), "=f"(u0o.z), "=f"(u0o.w)
@@ -319,8 +327,9 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
         // kappa of row i, read once: the B levels take it from a register ring
         // of kU rows (slot K) at the next B steps.  x-strip CTAs, whose 260
         // threads leave 168 registers a thread, and the whole-sweep kernel
-        // (whose pass loop needs the registers) read it per level instead.
-        if constexpr (XH == 0 && !SWEEP) {
+        // (SWEEP 1, whose pass loop needs the registers) read it per level
+        // instead.
+        if constexpr (XH == 0 && SWEEP != 1) {
             const float4 kq = *(const float4*)((const float*)S::deep(sm, dslot(K)) + kCpt * t);
             KR[K][0] = kq.x;
             KR[K][1] = kq.y;
@@ -403,7 +412,7 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
         float dn[kCpt], vn[kCpt];
         if (MID || l < L) {
             float kk[4];
-            if constexpr (XH == 0 && !SWEEP) {
+            if constexpr (XH == 0 && SWEEP != 1) {
 #pragma unroll
                 for (int k = 0; k < kCpt; ++k) kk[k] = KR[(K + 2 * kU - 1 - l) % kU][k];
             } else {
@@ -596,7 +605,7 @@ __device__ __forceinline__ bool tb2d_step(const Tb2dParams& p, const Seg& sg, un
     }
     // one barrier per row; it also makes the abort decision uniform
     if constexpr (GB == 0) return __syncthreads_or(timed_out) != 0;
-    else return group_or<GB>(timed_out);
+    else return group_or<GB>(timed_out, 1 + grp);
 }
 
 // XH = 0: a CTA holds whole periodic rows (n = 4 NT).  XH > 0: it holds
@@ -628,17 +637,18 @@ __device__ __forceinline__ void tb2d_init_bars(unsigned char* sm) {
 // One pass of B levels (or p.levels in the general variant) over the rows
 // [r_begin, r_end) of the pass's row space (rows_total = slices x strips x
 // n), continuing the ring at position `pos` (a multiple of kU; advanced past
-// the pass).  Run by threads 0 .. NT-1 of the CTA: GB = 0, the whole CTA,
-// which is NT threads; GB = NT, the first NT threads (whole warps) of a larger
-// CTA, whose per-row barrier is then the named barrier 1.  Returns true if a
-// bounded wait gave up.
-template <int NT, int B, int XH, bool MID, bool HALF0, int CL, bool SWEEP, int GB>
+// the pass).  GB = 0: run by the whole CTA, which is NT threads.  GB = NT:
+// run by thread group `grp` of a larger CTA (threads grp NT .. grp NT + NT-1,
+// whole warps), whose shared memory `sm` is the group's own and whose
+// per-row barrier is the named barrier 1 + grp.  Returns true if a bounded
+// wait gave up.
+template <int NT, int B, int XH, bool MID, bool HALF0, int CL, int SWEEP, int GB>
 __device__ __forceinline__ bool tb2d_rows(const Tb2dParams& p, unsigned char* sm, uint32_t& pos_io, int64_t r_begin,
-                                          int64_t r_end) {
+                                          int64_t r_end, int grp = 0) {
     static_assert(CL == 1 || (CL == 2 && XH == 0), "rows are shared by at most two CTAs, without x-strips");
     static_assert(GB == 0 || (GB == NT && CL == 1), "a thread group holds whole rows or x-strips alone");
     using S = Smem<NT, B>;
-    const int t = threadIdx.x;
+    const int t = GB == 0 ? (int)threadIdx.x : (int)threadIdx.x - grp * GB;
     const int n = p.n;
     const int64_t pts = (int64_t)n * n;
     const int L = MID ? B : p.levels;
@@ -715,7 +725,7 @@ __device__ __forceinline__ bool tb2d_rows(const Tb2dParams& p, unsigned char* sm
 #define PR_TB2D_STEP(K)                                                                                   \
     if (i >= niter) break;                                                                                 \
     if (tb2d_step<NT, B, XH, MID, HALF0, CL, K, SWEEP, GB>(p, sg, sm, i, par, R, VV, UH, KR, DR, timed_out, consumed, \
-                                               issued_end, pol, pr)) {                                     \
+                                               issued_end, pol, pr, grp)) {                                \
         aborted = true;                                                                                    \
         break;                                                                                             \
     }                                                                                                      \
@@ -761,7 +771,7 @@ __device__ __forceinline__ bool tb2d_rows(const Tb2dParams& p, unsigned char* sm
 
 // One pass over this CTA's (cluster's) share of the rows of the whole pass:
 // contiguous ranges of equal cost, rows + (L + B) steps per segment.
-template <int NT, int B, int XH, bool MID, bool HALF0, int CL, bool SWEEP>
+template <int NT, int B, int XH, bool MID, bool HALF0, int CL, int SWEEP>
 __device__ __forceinline__ bool tb2d_pass(const Tb2dParams& p, unsigned char* sm, uint32_t& pos_io, bool skip) {
     const int L = MID ? B : p.levels;
     const int64_t unit = blockIdx.x / CL, units = gridDim.x / CL;

@@ -50,12 +50,13 @@ def balanced_rows(queries):
 
 def queue_plan(instances):
     """qplan::build of queue_plan.h for instances [(n, slices, m)], evaluated
-    by the compiled harness: (counters, passes, items), passes as tuples
+    by the compiled harness: (counters, passes, items, units), passes as tuples
     (inst, k, cls, g0, levels, strips) and items as (pass, vslice, dep, need)
-    in queue order; counters is -1 if the plan was refused."""
+    in queue order, and units (first, count) as the CTAs claim them;
+    counters is -1 if the plan was refused."""
     text = "".join(f"{n} {s} {m}\n" for n, s, m in instances)
     res = subprocess.run([harness(), "plan"], input=text, capture_output=True, text=True, check=True)
-    ndep, passes, items = None, [], []
+    ndep, passes, items, units = None, [], [], []
     for line in res.stdout.splitlines():
         tag, *vals = line.split()
         vals = [int(v) for v in vals]
@@ -65,4 +66,6 @@ def queue_plan(instances):
             passes.append(tuple(vals))
         elif tag == "I":
             items.append(tuple(vals))
-    return ndep, passes, items
+        elif tag == "U":
+            units.append(tuple(vals))
+    return ndep, passes, items, units

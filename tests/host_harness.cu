@@ -6,7 +6,8 @@
 //   plan           the batch work-queue plan (queue_plan.h): reads
 //                  "n slices m" lines (one instance each) on stdin, prints
 //                  "P inst k cls g0 levels strips" per pass, then
-//                  "I pass vslice dep need" per item in queue order.
+//                  "I pass vslice dep need" per item in queue order, then
+//                  "U first count" per unit (what one CTA claims).
 #include <cstdio>
 #include <cstring>
 
@@ -21,11 +22,13 @@ int main(int argc, char** argv) {
         while (std::scanf("%lld %d %d", &n, &slices, &m) == 3) inst.push_back({n, slices, m});
         std::vector<qplan::Pass> passes;
         std::vector<qplan::Item> items;
-        const int ndep = qplan::build(inst, &passes, &items);
+        std::vector<qplan::Unit> units;
+        const int ndep = qplan::build(inst, &passes, &items, &units);
         std::printf("D %d\n", ndep);
         for (const auto& p : passes)
             std::printf("P %d %d %d %d %d %d\n", p.inst, p.k, p.cls, p.g0, p.levels, p.strips);
         for (const auto& it : items) std::printf("I %d %d %d %u\n", it.pass, it.vslice, it.dep, it.need);
+        for (const auto& u : units) std::printf("U %d %d\n", u.first, u.count);
         return 0;
     }
     long long rows, b, G;

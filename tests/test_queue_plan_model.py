@@ -18,7 +18,7 @@ def _passes_of(passes, inst):
 
 def test_level_split_covers_every_level_in_fused_passes():
     ms = list(range(8, 140)) + [255, 256, 257, 383, 384, 385, 2047, 2048]
-    ndep, passes, _ = _shipped.queue_plan([(256, 1, m) for m in ms])
+    ndep, passes, _, _ = _shipped.queue_plan([(256, 1, m) for m in ms])
     assert ndep == len(ms)
     for i, m in enumerate(ms):
         ps = _passes_of(passes, i)
@@ -33,7 +33,7 @@ def test_level_split_covers_every_level_in_fused_passes():
 
 
 def test_classes_and_strips_cover_the_rows():
-    ndep, passes, _ = _shipped.queue_plan([(256, 2, 9), (512, 2, 9), (1024, 2, 9), (2048, 2, 9)])
+    ndep, passes, _, _ = _shipped.queue_plan([(256, 2, 9), (512, 2, 9), (1024, 2, 9), (2048, 2, 9)])
     assert ndep == 8
     cls = {p[0]: (p[2], p[5]) for p in passes}
     assert cls == {0: (0, 1), 1: (1, 1), 2: (2, 1), 3: (3, 3)}
@@ -48,8 +48,15 @@ def test_refuses_unsupported_instances():
 
 
 def _check_queue(instances, workers, seed):
-    ndep, passes, items = _shipped.queue_plan(instances)
+    ndep, passes, items, units = _shipped.queue_plan(instances)
     assert ndep == sum(s for _, s, _ in instances)
+    # units: consecutive items of one pass, as many as the class runs side by
+    # side (four at n = 256, two at 512, one at 1024 and 2048)
+    groups = {0: 4, 1: 2, 2: 1, 3: 1}
+    assert units[0][0] == 0 and sum(c for _, c in units) == len(items)
+    for (a, ca), (b, _) in zip(units, units[1:] + [(len(items), 0)]):
+        assert a + ca == b and 1 <= ca <= groups[passes[items[a][0]][2]]
+        assert len({items[j][0] for j in range(a, a + ca)}) == 1
     # coverage: every (pass, slice, strip) exactly once, counters per slice
     seen = collections.Counter((it[0], it[1]) for it in items)
     want = {(j, v) for j, p in enumerate(passes) for v in range(instances[p[0]][1] * p[5])}
@@ -63,29 +70,32 @@ def _check_queue(instances, workers, seed):
     for pj, v, dep, need in items:
         assert before[dep] >= need
         before[dep] += 1
-    # claims in queue order by `workers` CTAs with random item durations:
-    # every claimed item eventually starts, so the queue drains
+    # claims of whole units in queue order by `workers` CTAs with random
+    # durations: a unit starts once every item's counter is met (the CTA's
+    # leader waits for each), and every claimed unit eventually starts, so
+    # the queue drains
     rng = np.random.default_rng(seed)
     cnt = collections.Counter()
     nxt = 0
-    running = []           # (finish time, dep) of started items
-    waiting = []           # (dep, need) of claimed items not yet startable
+    running = []           # (finish time, deps) of started units
+    waiting = []           # [(dep, need)] of claimed units not yet startable
     t = 0.0
     free = workers
-    while nxt < len(items) or running or waiting:
-        while free > 0 and nxt < len(items):
-            _, _, dep, need = items[nxt]
+    while nxt < len(units) or running or waiting:
+        while free > 0 and nxt < len(units):
+            a, ca = units[nxt]
             nxt += 1
             free -= 1
-            waiting.append((dep, need))
-        started = [w for w in waiting if cnt[w[0]] >= w[1]]
-        waiting = [w for w in waiting if cnt[w[0]] < w[1]]
-        for dep, _ in started:
-            running.append((t + rng.uniform(0.5, 2.0), dep))
-        assert running, "every claimed item waits for an item behind it"
-        running.sort()
-        t, dep = running.pop(0)
-        cnt[dep] += 1
+            waiting.append([(items[j][2], items[j][3]) for j in range(a, a + ca)])
+        ready = [w for w in waiting if all(cnt[d] >= nd for d, nd in w)]
+        waiting = [w for w in waiting if not all(cnt[d] >= nd for d, nd in w)]
+        for w in ready:
+            running.append((t + rng.uniform(0.5, 2.0), [d for d, _ in w]))
+        assert running, "every claimed unit waits for an item behind it"
+        running.sort(key=lambda r: r[0])
+        t, deps = running.pop(0)
+        for d in deps:
+            cnt[d] += 1
         free += 1
     return passes, items
 
