@@ -74,10 +74,11 @@ struct Unit {
     int first, count;
 };
 
-// Passes of every instance, and the items in queue order: pass k of an
-// instance of P passes has the key (k + 1/2) / P (instances interleaved by
-// progress; ties keep instance order), then its slices and strips in order,
-// cut into units of the class's group count.  Pass k of a slice needs
+// Passes of every instance, and the items in queue order: the widest class
+// first, and within a class pass k of an instance of P passes at the key
+// (k + 1/2) / P (instances interleaved by progress; ties keep instance
+// order); then the pass's slices and strips in order, cut into units of the
+// class's group count.  Pass k of a slice needs
 // k * strips completions of the slice's counter, one per item of each
 // earlier pass.  Returns the number of counters, or -1 if an instance has no
 // class or fewer than 8 steps.
@@ -99,7 +100,7 @@ inline int build(const std::vector<Inst>& inst, std::vector<Pass>* passes, std::
         const auto plan = level_plan(inst[i].m);
         const int P = (int)plan.size();
         for (int k = 0; k < P; ++k) {
-            order.push_back({(k + 0.5) / P, (int)passes->size()});
+            order.push_back({(3 - c) + (k + 0.5) / P, (int)passes->size()});
             passes->push_back({i, k, c, plan[k].first, plan[k].second, strips_of(c), k == 0, k == P - 1});
             dep_base.push_back(ndep);
         }

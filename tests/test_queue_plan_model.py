@@ -108,12 +108,18 @@ def test_queue_drains_for_any_number_of_ctas(workers):
 
 def test_full_uneven_workload_queue():
     """The 48 seeded instances of the uneven batch: coverage, order and a
-    152-CTA claim simulation, and the interleaving by progress (the longest
-    pass chain starts in the first hundredth of the queue and ends in the
-    last)."""
+    152-CTA claim simulation; the widest class first, and within a class the
+    interleaving by progress (the longest pass chain of the class starts in
+    the first hundredth of the class's items and ends in the last)."""
     ws = [W.config4_instance(i) for i in range(48)]
     inst = [(w.n_fine, w.n_slices, w.m_f) for w in ws]
     passes, items = _check_queue(inst, 152, seed=48)
-    longest = max(range(48), key=lambda i: len(_passes_of(passes, i)))
-    pos = [q for q, it in enumerate(items) if passes[it[0]][0] == longest]
-    assert pos[0] < len(items) // 100 and pos[-1] > len(items) * 99 // 100
+    cls = [passes[it[0]][2] for it in items]
+    assert cls == sorted(cls, reverse=True)
+    for c in set(cls):
+        span = [q for q, k in enumerate(cls) if k == c]
+        members = {passes[it[0]][0] for it in items[span[0]:span[-1] + 1]}
+        longest = max(members, key=lambda i: len(_passes_of(passes, i)))
+        pos = [q for q in span if passes[items[q][0]][0] == longest]
+        a, b = span[0], span[-1] + 1
+        assert pos[0] - a < (b - a) // 100 + 1 and pos[-1] - a >= (b - a) * 99 // 100, (c, pos[0], pos[-1], a, b)
