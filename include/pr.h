@@ -349,9 +349,11 @@ typedef struct pr_batch pr_batch;
  * Then captures all sweeps into one CUDA graph: one branch per instance,
  * biggest first, spread over 8 library-owned streams between a fork and a
  * join (one launch per pass: pr_set_one_launch is switched off for the
- * bound contexts, whose sweeps run concurrently).  Runs (and synchronises) the timing sweeps; the bound arrays must
- * stay valid until pr_batch_destroy.  The contexts must not be used
- * concurrently with a launch of the batch.  PR_EINVAL if a context appears
+ * bound contexts, whose sweeps run concurrently).  Runs (and synchronises)
+ * the timing sweeps.  The bound arrays and the contexts (whose scratch, kappa
+ * and error flags the graph uses) must stay valid while the batch is
+ * launched; the contexts must not be used concurrently with a launch of the
+ * batch.  PR_EINVAL if a context appears
  * twice or an output array overlaps an array of another instance (inputs may
  * be shared between instances; in == out within one instance is allowed). */
 pr_status pr_batch_create(int count, pr_ctx* const* ctxs, const void* const* u_in,

@@ -246,7 +246,9 @@ __global__ void __launch_bounds__(kQT, 1) batch_queue_kernel(const QParams qp) {
 }  // namespace
 
 struct pr_queue {
-    pr_ctx* owner = nullptr;   // the first instance's context: its allocator holds the tables
+    // the first instance's caller allocator (copied: the tables may outlive
+    // that context), which holds the tables
+    pr_ctx owner;
     int device = 0;
     QItem* items = nullptr;
     QUnit* units = nullptr;
@@ -268,12 +270,12 @@ bool pr_queue_supported(const pr_ctx* c) {
 
 void pr_queue_destroy(pr_queue* q) {
     if (!q) return;
-    pr_dev_free(q->owner, q->items);
-    pr_dev_free(q->owner, q->units);
-    pr_dev_free(q->owner, q->passes);
-    pr_dev_free(q->owner, q->ctr);
-    pr_dev_free(q->owner, q->stop);
-    pr_dev_free(q->owner, q->flags);
+    pr_dev_free(&q->owner, q->items);
+    pr_dev_free(&q->owner, q->units);
+    pr_dev_free(&q->owner, q->passes);
+    pr_dev_free(&q->owner, q->ctr);
+    pr_dev_free(&q->owner, q->stop);
+    pr_dev_free(&q->owner, q->flags);
     delete q;
 }
 
@@ -332,17 +334,19 @@ pr_status pr_queue_create(int count, pr_ctx* const* ctx, const void* const* ui, 
     for (const qplan::Unit& un : qunits) units.push_back({un.first, un.count});
 
     pr_queue* q = new pr_queue();
-    q->owner = ctx[0];
+    q->owner.ualloc = ctx[0]->ualloc;
+    q->owner.urelease = ctx[0]->urelease;
+    q->owner.uarg = ctx[0]->uarg;
     cudaGetDevice(&q->device);
     q->nunits = (int)units.size();
     q->wait_ns = wait_ns;
     q->ctr_bytes = (1 + (size_t)ndep) * sizeof(unsigned);
-    cudaError_t e = pr_dev_malloc(q->owner, (void**)&q->items, items.size() * sizeof(QItem));
-    if (e == cudaSuccess) e = pr_dev_malloc(q->owner, (void**)&q->units, units.size() * sizeof(QUnit));
-    if (e == cudaSuccess) e = pr_dev_malloc(q->owner, (void**)&q->passes, passes.size() * sizeof(QPass));
-    if (e == cudaSuccess) e = pr_dev_malloc(q->owner, (void**)&q->ctr, q->ctr_bytes);
-    if (e == cudaSuccess) e = pr_dev_malloc(q->owner, (void**)&q->stop, sizeof(int));
-    if (e == cudaSuccess) e = pr_dev_malloc(q->owner, (void**)&q->flags, count * sizeof(int*));
+    cudaError_t e = pr_dev_malloc(&q->owner, (void**)&q->items, items.size() * sizeof(QItem));
+    if (e == cudaSuccess) e = pr_dev_malloc(&q->owner, (void**)&q->units, units.size() * sizeof(QUnit));
+    if (e == cudaSuccess) e = pr_dev_malloc(&q->owner, (void**)&q->passes, passes.size() * sizeof(QPass));
+    if (e == cudaSuccess) e = pr_dev_malloc(&q->owner, (void**)&q->ctr, q->ctr_bytes);
+    if (e == cudaSuccess) e = pr_dev_malloc(&q->owner, (void**)&q->stop, sizeof(int));
+    if (e == cudaSuccess) e = pr_dev_malloc(&q->owner, (void**)&q->flags, count * sizeof(int*));
     std::vector<int*> flags(count);
     for (int i = 0; i < count; ++i) flags[i] = ctx[i]->dev_flag;
     q->ninst = count;
