@@ -366,7 +366,11 @@ pr_status pr_queue_create(int count, pr_ctx* const* ctx, const void* const* ui, 
         pr_queue_destroy(q);
         return pr_cuda_fail(nullptr, e, "pr_batch (queue): setup");
     }
-    q->grid = std::max(1, per_sm * sms);
+    if (per_sm < 1 || sms < 1) {
+        pr_queue_destroy(q);
+        return pr_fail(nullptr, PR_ECUDA, "pr_batch (queue): the kernel does not fit on an SM");
+    }
+    q->grid = per_sm * sms;
     *out = q;
     return PR_OK;
 }
