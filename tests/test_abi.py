@@ -49,6 +49,14 @@ def test_null_arguments_are_rejected_without_a_device(libpath):
     assert b"NULL" in lib.pr_last_error(None)
     assert lib.pr_fine_all_slices(None, None, None, None, None, 0, 1, None) == 1
     lib.pr_destroy(None)
+    # the batch entry points refuse a missing batch or an empty instance list
+    bout = ctypes.c_void_p()
+    assert lib.pr_batch_create(0, None, None, None, None, None, 0, None, ctypes.byref(bout)) == 1
+    assert bout.value is None
+    assert lib.pr_batch_launch(None, None) == 1
+    assert lib.pr_batch_set_mode(None, 1, None, None) == 1
+    assert lib.pr_batch_info(None, 0, None, None, None) == 1
+    lib.pr_batch_destroy(None)
 
 
 def test_noalloc_binding_rejects_unequal_axes_before_any_launch():
