@@ -1,38 +1,42 @@
 // One persistent kernel for a batch of independent 2D FP32 instances of uneven
 // sizes (Alg. 3's parFor over slices, for many problems at once): every fused
 // pass of every slice of every instance is a work item in a device queue, and
-// a grid of one CTA per SM claims items in queue order until the queue is
+// a grid of one CTA per SM claims them in queue order until the queue is
 // empty.
 //
 // Items.  An item is one pass (B = 8 levels, or fewer in the last passes) over
 // one slice of one instance, or over one x-strip of a slice at n = 2048: the
 // pass bodies are those of the per-pass kernels (tb2d_kernels.cuh), run by a
-// thread group of the CTA that holds the item's rows alone:
+// thread group that holds the item's rows alone:
 //   n = 256   64 threads, whole rows         n = 512   128 threads
 //   n = 1024  256 threads                    n = 2048  192 threads, x-strips of
 //                                                      768 columns (752 final)
-// The rest of the CTA's warps wait at the item's closing barrier.
+// A CTA claims a unit: consecutive items of one pass, as many as its groups
+// run side by side (four at n = 256, two at 512, one otherwise), each group
+// on its own shared memory with its own named row barrier.  Warps without an
+// item wait at the unit's closing barrier.
 //
 // Order.  Pass k of a slice reads what pass k-1 wrote for the whole slice
 // (the y-halo, and at n = 2048 the x-halo of the neighbouring strips), so
-// each (instance, slice) has a completion counter and an item waits (bounded)
-// until the counter shows every item of the slice's previous pass.  Items are
-// claimed in queue order, and the queue is a topological order (the passes of
-// an instance in sequence), so an item only ever waits for items that CTAs
-// already hold: no co-residency of the grid is needed.  Instances are
-// interleaved by progress, the key of pass k of an instance of P passes being
-// (k + 1/2) / P, so that the long pass chains (few slices, many steps each)
-// run alongside the wide ones instead of after them.
+// each (instance, slice) has a completion counter and a unit waits (bounded)
+// until the counters show every item of its slices' previous pass.  Units
+// are claimed in queue order, and the queue is a topological order (the
+// passes of an instance in sequence), so a unit only ever waits for items
+// that CTAs already hold: no co-residency of the grid is needed.  The widest
+// class comes first; within a class, instances are interleaved by progress,
+// the key of pass k of an instance of P passes being (k + 1/2) / P, so that
+// the long pass chains (few slices, many steps each) run alongside the wide
+// instances instead of after them (queue_plan.h).
 //
-// Visibility.  A finished item's stores are fenced for the async proxy and
-// released at GPU scope before its counter is incremented; the waiting CTA
-// acquires the counter and fences the async proxy before its bulk copies of
+// Visibility.  A finished unit's stores are fenced for the async proxy and
+// released at GPU scope before its counters are incremented; the waiting CTA
+// acquires the counters and fences the async proxy before its bulk copies of
 // the rows, and reads the finished row's u_hi past L1 (the whole-sweep form
-// of the pass body).
+// of the pass body: L1 is not coherent within one launch).
 //
-// Shared memory is the largest class's layout; the ring mbarriers of a class
-// live at that class's offsets, so a CTA invalidates and re-arms them when
-// consecutive items change class.
+// Shared memory is the largest of the classes' layouts (times their groups);
+// the ring mbarriers of a class live at that class's offsets, so a CTA
+// invalidates and re-arms them when consecutive units change class.
 #include <algorithm>
 #include <vector>
 
@@ -113,7 +117,8 @@ __device__ __forceinline__ void q_bars_of(unsigned char* sm, int c, bool arm) {
 
 // Retire the ring mbarriers of class `from` (none: -1) and arm those of
 // class `to`.  Every copy on the old ones has landed and been consumed: the
-// previous item closed its ring lap before the CTA's item barrier.
+// previous unit's items closed their ring laps before the unit's closing
+// barrier.
 __device__ __forceinline__ void q_switch(unsigned char* sm, int from, int to) {
     if (threadIdx.x == 0) {
         q_bars_of(sm, from, false);
