@@ -50,12 +50,15 @@ ALGO_BYTES_PER_POINT_PASS = 20  # read u, u_t, kappa + write u, u_t (FP32)
 FALLBACK_HBM_GBS = 6800.0
 
 
-def hbm_passes(m_f: int, depth: int) -> int:
+def hbm_passes(m_f: int, depth: int, merge_last: bool = True) -> int:
     """HBM passes of one sweep of m_f steps (m_f + 1 kick levels) at `depth`
-    levels per pass; a lone final level joins the last pass at depth 8."""
+    levels per pass.  At depth 8 a lone final level joins the last pass where
+    the fused kernel takes 9 levels (merge_last: whole rows of n <= 1024 at
+    four columns per thread); elsewhere it is a pass of its own, and the
+    work-queue batch kernel splits the last 9 levels as 5 + 4."""
     levels = m_f + 1
     passes = -(-levels // depth)
-    if depth == 8 and passes >= 2 and levels % depth == 1:
+    if merge_last and depth == 8 and passes >= 2 and levels % depth == 1:
         passes -= 1
     return passes
 
@@ -444,10 +447,12 @@ def run_batch(a) -> int:
     # roofline of the whole graph: every instance's algorithmic traffic (20 B
     # per point per HBM pass) over the graph's time per step
     depths = [batch.info(i)[0] for i in range(len(ws))]
+    cols = [batch.info(i)[1] for i in range(len(ws))]
     if mode == 1:   # the queue kernel: passes of 8 levels (a lone last level splits as 5 + 4)
-        passes = [-(-(w.m_f + 1) // 8) for w in ws]
+        passes = [hbm_passes(w.m_f, 8, merge_last=False) for w in ws]
     else:
-        passes = [hbm_passes(w.m_f, d) for w, d in zip(ws, depths)]
+        passes = [hbm_passes(w.m_f, d, merge_last=(w.n_fine <= 1024 and c in (0, 4)))
+                  for w, d, c in zip(ws, depths, cols)]
     step_bytes = sum(ALGO_BYTES_PER_POINT_PASS * w.points * w.n_slices * pz for w, pz in zip(ws, passes))
     peak, peak_src = measured_peak()
     achieved = step_bytes / (ms / a.steps * 1e-3) / 1e9

@@ -24,6 +24,21 @@ def test_workload_selection():
             bench.workload_for(bad)
 
 
+def test_pass_counts():
+    # 385 levels at depth 8: the lone last level joins the 48th pass where
+    # the fused kernel takes 9 levels, else it is a 49th
+    assert bench.hbm_passes(384, 8) == 48
+    assert bench.hbm_passes(384, 8, merge_last=False) == 49
+    assert bench.hbm_passes(383, 8) == 48 and bench.hbm_passes(64, 4) == 17 and bench.hbm_passes(7, 1) == 8
+    # the work-queue kernel's plan (queue_plan.h, through the host harness)
+    # has as many passes as the unmerged count
+    from tests import _shipped
+    ms = [8, 9, 15, 16, 17, 255, 256, 512, 2036]
+    _, passes, _, _ = _shipped.queue_plan([(256, 1, m) for m in ms])
+    for i, m in enumerate(ms):
+        assert sum(1 for p in passes if p[0] == i) == bench.hbm_passes(m, 8, merge_last=False), m
+
+
 def test_kernel_hash_ignores_comments_but_not_code():
     src = {rel: open(os.path.join(bench.ROOT, rel)).read() for rel in bench.KERNEL_SOURCES}
     base = bench.kernel_source_hash(lambda rel: src[rel])
